@@ -1,0 +1,197 @@
+/*
+ * bse.h - C ABI of the GB300 double-grid BSE Haydock library.
+ *
+ * The library computes the macroscopic dielectric function of the
+ * Bethe-Salpeter equation in the Tamm-Dancoff approximation (Sec. 2,
+ * Eqs. bse1, epsmacro) with the Lanczos-Haydock recursion (Eqs. ai, bi, ci)
+ * and its continued fraction (Eq. fraccont).  Every Lanczos step applies the
+ * dense-mesh Hamiltonian H = diag(Delta E) + K^i, with K^i interpolated on
+ * the fly from the coarse-mesh kernel K_c (Sec. 4, Eqs. interpmatmul,
+ * matmul1-matmul3: restrict -> K_c apply -> prolong), optionally with the
+ * near-diagonal treatment of the small-q divergence ("Method 3", Sec. 4,
+ * Eq. diverg).
+ *
+ * Conventions shared by every call
+ *   - All functions are extern "C", thread-compatible (one context per host
+ *     thread), and return an int status: 0 = BSE_OK, < 0 an error, > 0 a
+ *     warning.  bse_last_error(ctx) returns a message for the last failure.
+ *   - "host" pointers are read or written during the call only.  "device"
+ *     pointers are CUDA global-memory addresses on the context's device
+ *     (e.g. torch tensor data_ptr()); the caller keeps them alive for the
+ *     call.  Handles own their device memory and free it in bse_free_*.
+ *   - Complex numbers are interleaved (re, im) pairs: double2 for complex128,
+ *     float2 for complex64.
+ *   - Meshes (Sec. 3): coarse k~_(i) = i / n, i in [0, n)^3, coarse index
+ *     ic = (i1 n + i2) n + i3.  Dense k = (i + j / n_div) / n, j in
+ *     [0, n_div)^3, dense index coarse-major kd = ic * n_div^3 + js,
+ *     js = (j1 n_div + j2) n_div + j3.  Transition index tr = v * nc + c.
+ *     A vector of the transition space has N = t * N_k entries, t = nv * nc,
+ *     element kd * t + tr.
+ *   - There is no CPU fallback: without a CUDA device every call that needs
+ *     one returns BSE_ERR_CUDA.
+ */
+#ifndef BSE_H
+#define BSE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----------------------------------------------------------- status codes */
+#define BSE_OK                0
+#define BSE_ERR_ARG          -1   /* bad size, pointer, flag or non-finite input  */
+#define BSE_ERR_OOM          -2   /* device allocation failed                    */
+#define BSE_ERR_CUDA         -3   /* CUDA runtime error (message has the detail) */
+#define BSE_ERR_TIMEOUT      -4   /* a bounded device wait gave up               */
+#define BSE_ERR_UNSUPPORTED  -5   /* combination not built (e.g. size limits)    */
+#define BSE_WARN_BREAKDOWN    1   /* some chain stopped early: b_{i+1} ~ 0       */
+
+/* -------------------------------------------------------------- precisions */
+#define BSE_PREC_F64   0   /* complex128 storage / FP64 arithmetic                  */
+#define BSE_PREC_F32   1   /* complex64 storage / FP32 arithmetic                   */
+#define BSE_PREC_BF16  2   /* K_c as separate BF16 real and imaginary planes,
+                              applied on the tensor cores with FP32 accumulation   */
+
+/* ----------------------------------------------------------------- schemes */
+#define BSE_SCHEME_M1   0  /* Method 1: interpolation everywhere (Sec. 4)           */
+#define BSE_SCHEME_M3   1  /* Method 3: M1 plus divergence treatment on near pairs  */
+#define BSE_NB1        16  /* OR-flag: one-neighbour weights (Eq. eqRL, f = 1 on
+                              the nearest coarse corner) instead of trilinear 8NB   */
+
+/* ------------------------------------------------------------ Haydock flags */
+#define BSE_REORTH_CGS2   1  /* full reorthogonalisation, classical Gram-Schmidt x2 */
+#define BSE_USE_GRAPH     2  /* capture the step loop in a CUDA graph (cached)      */
+#define BSE_PROFILE       4  /* time the kernel classes with events (see
+                                bse_last_kernel_times)                              */
+
+/* Synthetic model crystal (stand-in for the ab initio inputs of Sec. 2,
+ * Eqs. bse2-bse3b).  All arrays are host, row-major, complex interleaved:
+ *   offsets [nv][nc]          real, eV
+ *   gen_v   [3][2][nv][nv]    Hermitian gauge generators (axis, kind sin / 1-cos)
+ *   gen_c   [3][2][nc][nc]
+ *   mu      [7][26][nv][nc]   exchange form-factor coefficients per k-harmonic
+ *                             (1, cos 2pi k1, sin 2pi k1, cos k2, sin k2, cos k3,
+ *                             sin k3) and non-zero G in {-1,0,1}^3 (lexicographic)
+ *   dip     [7][3][nv][nc]    dipole coefficients per harmonic and direction
+ * Band gauge U_b(k) = expm(i sum_a [sin(2 pi k_a) gen[a][0] + (1 - cos 2 pi k_a) gen[a][1]]);
+ * overlaps d = U(k~)^H U(k) (Eq. completeness); kernel on a grid of N_g points
+ *   K = (e_k / N_g) [ 2 sum_{G!=0} (4 pi / |G|^2) conj(M_vc(k,G)) M_v'c'(k',G)
+ *                     - (1 / eps_inf) O^v_vv'(k,k') O^c_cc'(k,k') h(k - k') ],
+ * M = U_v^H mu U_c, O^v = U_v(k)^T conj(U_v(k')), O^c = U_c(k)^H U_c(k'),
+ * h(q) = sum_G exp(-|G|^2) 4 pi / (|q + G|^2 + kappa^2) over direct_shells G
+ * (27 or the G = 0 shell only), q the minimum image (ties averaged), or
+ * h = h0 when h_const.  Delta E_vc(k) = e_gap + band_width sum_i (1 - cos 2 pi k_i)
+ * + offsets[v][c].  Dipoles P_vc = [U_v^T pi(k) conj(U_c)]_vc.                  */
+typedef struct bse_model {
+    int nv, nc;
+    double eps_inf, kappa, e_k, e_gap, band_width;
+    int direct_shells;        /* 27 or 1 */
+    int h_const;              /* 0 / 1   */
+    double h0;
+    int exchange_on;          /* 0 / 1   */
+    const double* offsets;
+    const double* gen_v;
+    const double* gen_c;
+    const double* mu;
+    const double* dip;
+} bse_model;
+
+typedef struct bse_ctx bse_ctx;
+typedef struct bse_coarse bse_coarse;
+typedef struct bse_interp bse_interp;
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int bse_version(void);
+
+/* Create a context on `device`.  `cuda_stream` is a cudaStream_t (e.g. a
+ * torch.cuda.Stream's cuda_stream); every kernel and copy of the context is
+ * issued on it.  NULL makes the context create (and later destroy) a blocking
+ * stream of its own, ordered with the legacy default stream.  Returns
+ * BSE_ERR_CUDA when no device is present. */
+int bse_ctx_create(bse_ctx** out, int device, void* cuda_stream);
+void bse_ctx_destroy(bse_ctx* ctx);
+const char* bse_last_error(const bse_ctx* ctx);
+
+/* Coarse-mesh BSE data (Sec. 3-4): builds on the device the band gauge at the
+ * n^3 coarse points, the coarse kernel K_c (Eq. bse2 with the model of
+ * bse_model, dimension N_c = t n^3, Hermitian) stored in `kc_prec`
+ * (BSE_PREC_F64 complex128, BSE_PREC_F32 complex64, BSE_PREC_BF16 planes),
+ * and the head factors of Eq. diverg (the G = 0 direct term,
+ * A_c = alpha O^v (x) O^c with alpha = -(e_k / n^3) 4 pi / eps_inf).
+ * Errors: BSE_ERR_ARG (nv, nc outside 1..8, n < 1, non-finite model numbers,
+ * direct_shells not 1 or 27), BSE_ERR_OOM, BSE_ERR_CUDA. */
+int bse_build_coarse(bse_ctx* ctx, const bse_model* model, int n_coarse, int kc_prec,
+                     bse_coarse** out);
+/* Copy K_c to host as complex128 [N_c][N_c] (converted from its storage). */
+int bse_coarse_get_kc(bse_ctx* ctx, const bse_coarse* coarse, double* host_kc);
+void bse_free_coarse(bse_coarse* coarse);
+
+/* Interpolation set-up for one dense mesh refining `coarse` by n_div per
+ * axis (Sec. 3): dense Delta E (exact on the dense mesh), dipoles P^alpha,
+ * band overlaps d for every (dense k, coarse corner) with a non-zero weight
+ * (Eq. completeness, v-c mixing neglected as in Sec. 5.1), trilinear or
+ * one-neighbour weights (Eqs. interpwfn, eqRL), and for BSE_SCHEME_M3 the
+ * near-pair tables: pairs with ||k - k'|| <= width_w * d, d one coarse
+ * spacing, tested on the integer dense offset delta as
+ * |delta|^2 <= floor(width_w^2 n_div^2 + 1e-9).
+ * `vec_prec` (F64 or F32) is the precision of the Lanczos vectors and of the
+ * restrict / prolong / near-field arithmetic; Lanczos reductions are FP64
+ * in every mode.  The coarse handle must outlive the interp handle.
+ * Errors: BSE_ERR_ARG (n_div < 1; M3 with width_w >= n / 2, where the near
+ * region would wrap around the zone; bad flags), BSE_ERR_OOM, BSE_ERR_CUDA. */
+int bse_interp_setup(bse_ctx* ctx, const bse_coarse* coarse, int n_div, int scheme,
+                     double width_w, int vec_prec, bse_interp** out);
+void bse_free_interp(bse_interp* interp);
+
+/* Sizes of an interp handle: info[0] = N (dense dimension), [1] = N_k,
+ * [2] = N_c (coarse dimension), [3] = t, [4] = n, [5] = n_div,
+ * [6] = number of near offsets (M3, else 0), [7] = vec_prec. */
+int bse_interp_info(const bse_interp* interp, long long* info);
+
+/* Dipole start vectors P(e) = sum_alpha e_alpha P^alpha for `npol`
+ * directions (host [npol][3]) into device `p_out` [npol][N] in the interp's
+ * vector precision, and their squared norms (FP64) into host `pnorm2` [npol]. */
+int bse_dipoles(bse_ctx* ctx, bse_interp* interp, int npol, const double* pol_dirs,
+                void* p_out, double* pnorm2);
+
+/* One application y = H x of the interpolated dense Hamiltonian
+ * (Eqs. interpmatmul, matmul1-3, plus the M3 near-field when set up) to
+ * `nvec` (1..4) device vectors x [nvec][N] -> y [nvec][N] in the interp's
+ * vector precision.  Uses the handle's scratch; calls on the same handle
+ * must not overlap. */
+int bse_apply_h(bse_ctx* ctx, bse_interp* interp, int nvec, const void* x, void* y);
+
+/* Haydock recursion (Eqs. ai, bi, ci) for `nsys` systems sharing the context.
+ * System s runs npol[s] (1..4) chains starting from P(e) for the directions
+ * pol_dirs (host, 3 doubles per chain, systems in order).  nsteps Lanczos
+ * steps per chain.  Outputs (host, chains in order):
+ *   a          [chains][nsteps]       a_1 .. a_m
+ *   b          [chains][nsteps + 1]   b_1 = 0, b_2 .. b_{m+1}
+ *   pnorm2     [chains]               ||P||^2
+ *   steps_done [chains]               m, or fewer after a breakdown
+ * flags: BSE_REORTH_CGS2, BSE_USE_GRAPH, BSE_PROFILE.  A chain whose
+ * b_{i+1} < 1e-12 max|a| stops there (BSE_WARN_BREAKDOWN).  Device waits
+ * are bounded; a wait that gives up returns BSE_ERR_TIMEOUT. */
+int bse_haydock_run(bse_ctx* ctx, bse_interp* const* sys, int nsys, const int* npol,
+                    const double* pol_dirs, int nsteps, int flags, double* a, double* b,
+                    double* pnorm2, int* steps_done);
+
+/* Kernel-class device times of the last BSE_PROFILE run, averaged per
+ * launch, in ms: [0] restrict, [1] K_c apply, [2] prolong+diagonal,
+ * [3] M3 near field, [4] Lanczos vector updates; counts[] launches. */
+int bse_last_kernel_times(const bse_ctx* ctx, double* ms_per_launch, long long* counts);
+
+/* Continued fraction (Eq. fraccont) on the device, FP64, bottom-up,
+ * truncated after steps_done[c] levels:
+ *   eps_c(w) = 1 - prefactor * pnorm2[c] * g_1(w + i eta)
+ * a [nchains][nsteps], b [nchains][nsteps + 1] as returned by
+ * bse_haydock_run; omega [nw]; eps out [nchains][nw] complex128.  All host. */
+int bse_spectrum(bse_ctx* ctx, int nchains, int nsteps, const int* steps_done,
+                 const double* a, const double* b, const double* pnorm2, double prefactor,
+                 double eta, int nw, const double* omega, double* eps);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BSE_H */

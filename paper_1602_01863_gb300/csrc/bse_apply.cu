@@ -1,0 +1,791 @@
+// Hot path: one interpolated H application per Lanczos step and the Lanczos
+// vector updates (Sec. 2 Eqs. ai-ci; Sec. 4 Eqs. matmul1-matmul3, M3).
+//
+//   restrict   Q(k~) = sum_{uvw} sum_{k' in S(k~ - uvw)} f conj(Dv) psi Dc^T     (Eq. matmul1,
+//              gathered per target coarse point by Eq. ordersums: no atomics)
+//   K_c apply  R = K_c Q                                                         (Eq. matmul2)
+//   near field u(k, k~) = sum_{k~'} A(k~,k~') [y1(k,k~') - h_head(q_c) z(k,k~')]  (M3)
+//   prolong    w = dE psi + (1/N_div) sum_l f Dv^T (R(k~_l) + u(k,l)) conj(Dc)    (Eqs. matmul3, bse1)
+//   Lanczos    a = Re<psi,w>, w -= a psi + b psi_prev, [CGS2], b' = ||w||, psi' = w / b'
+//
+// Every reduction is two-stage with a fixed order, so results are bitwise
+// reproducible run to run.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "bse_internal.cuh"
+
+namespace {
+
+constexpr int kRestrictWarps = 8;
+
+// ----------------------------------------------------------------- restrict
+// One CTA per target coarse point; warp w takes the (corner l, sub-point js)
+// pairs w, w + 8, ... with non-zero weight; lane e owns coarse transition e
+// (and e + 32).  OUT_BF16: write the split-BF16 operand of the tensor-core
+// apply (rows: Re hi, Im hi, Re lo, Im lo per chain) instead of Q.
+template <typename T, bool OUT_BF16>
+__global__ void __launch_bounds__(256) k_restrict(
+    const typename Cx<T>::V* __restrict__ psi, const typename Cx<T>::V* __restrict__ Dv,
+    const typename Cx<T>::V* __restrict__ Dc, int n, int nd, int nv, int nc, int nb1, int nchains,
+    int N, int Nc, typename Cx<T>::V* __restrict__ Q, __nv_bfloat16* __restrict__ Bop, int ldk,
+    typename Cx<T>::V* __restrict__ X, const int* __restrict__ stop) {
+    using V = typename Cx<T>::V;
+    __shared__ V red[kRestrictWarps][BSE_MAX_CHAINS][BSE_MAX_T];
+    const int t = nv * nc;
+    const int Ndiv = nd * nd * nd;
+    const int ic = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const Int3 i = unflat3(ic, n);
+    V acc[BSE_MAX_CHAINS][2];
+#pragma unroll
+    for (int ch = 0; ch < BSE_MAX_CHAINS; ++ch) { acc[ch][0] = czero<V>(); acc[ch][1] = czero<V>(); }
+    for (int p = warp; p < 8 * Ndiv; p += kRestrictWarps) {
+        const int l = p / Ndiv, js = p % Ndiv;
+        const T f = (T)interp_weight(js, l, nd, nb1);
+        if (f == (T)0) continue;
+        const int src = flat3(i.a - ((l >> 2) & 1), i.b - ((l >> 1) & 1), i.c - (l & 1), n);
+        const size_t kd = (size_t)src * Ndiv + js;
+        const V* dv = Dv + (kd * 8 + l) * nv * nv;
+        const V* dc = Dc + (kd * 8 + l) * nc * nc;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int e = lane + 32 * q;
+            if (e >= t) break;
+            const int n3 = e / nc, n4 = e % nc;
+            for (int ch = 0; ch < nchains; ++ch) {
+                const V* ps = psi + (size_t)ch * N + kd * t;
+                V x = czero<V>();
+                for (int vp = 0; vp < nv; ++vp) {
+                    V inner = czero<V>();
+                    for (int cp = 0; cp < nc; ++cp) inner = cadd(inner, cmul(ps[vp * nc + cp], dc[n4 * nc + cp]));
+                    x = cadd(x, cmulc(dv[n3 * nv + vp], inner));
+                }
+                x = cscale(x, f);
+                if (X) X[(((size_t)ch * (N / t) + kd) * 8 + l) * t + e] = x;
+                acc[ch][q] = cadd(acc[ch][q], x);
+            }
+        }
+    }
+    for (int ch = 0; ch < nchains; ++ch)
+        for (int q = 0; q < 2; ++q) {
+            const int e = lane + 32 * q;
+            if (e < t) red[warp][ch][e] = acc[ch][q];
+        }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nchains * t; idx += blockDim.x) {
+        const int ch = idx / t, e = idx % t;
+        V s = red[0][ch][e];
+        for (int w = 1; w < kRestrictWarps; ++w) s = cadd(s, red[w][ch][e]);
+        const int row = ic * t + e;
+        if (!OUT_BF16) {
+            Q[(size_t)ch * Nc + row] = s;
+        } else {
+            const float re = (float)s.x, im = (float)s.y;
+            const __nv_bfloat16 rh = __float2bfloat16_rn(re), ih = __float2bfloat16_rn(im);
+            const __nv_bfloat16 rl = __float2bfloat16_rn(re - __bfloat162float(rh));
+            const __nv_bfloat16 il = __float2bfloat16_rn(im - __bfloat162float(ih));
+            Bop[(size_t)(ch)*ldk + row] = rh;
+            Bop[(size_t)(nchains + ch) * ldk + row] = ih;
+            Bop[(size_t)(2 * nchains + ch) * ldk + row] = rl;
+            Bop[(size_t)(3 * nchains + ch) * ldk + row] = il;
+        }
+    }
+    (void)stop;
+}
+
+// ------------------------------------------------- K_c apply on CUDA cores
+// R[ch][i] = sum_j K[i][j] Q[ch][j]; one warp per row, fixed-order shuffle
+// reduction.  Used for complex128 and complex64 storage.
+template <typename T>
+__global__ void __launch_bounds__(256) k_kc_apply_simt(const typename Cx<T>::V* __restrict__ K,
+                                                      const typename Cx<T>::V* __restrict__ Q, int Nc,
+                                                      int nchains, typename Cx<T>::V* __restrict__ R) {
+    using V = typename Cx<T>::V;
+    const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= Nc) return;
+    V acc[BSE_MAX_CHAINS];
+#pragma unroll
+    for (int ch = 0; ch < BSE_MAX_CHAINS; ++ch) acc[ch] = czero<V>();
+    const V* kr = K + (size_t)row * Nc;
+    for (int j = lane; j < Nc; j += 32) {
+        const V k = kr[j];
+#pragma unroll
+        for (int ch = 0; ch < BSE_MAX_CHAINS; ++ch)
+            if (ch < nchains) acc[ch] = cadd(acc[ch], cmul(k, Q[(size_t)ch * Nc + j]));
+    }
+#pragma unroll
+    for (int ch = 0; ch < BSE_MAX_CHAINS; ++ch) {
+        if (ch >= nchains) break;
+        V v = acc[ch];
+        for (int off = 16; off > 0; off >>= 1) {
+            v.x += __shfl_xor_sync(0xffffffffu, v.x, off);
+            v.y += __shfl_xor_sync(0xffffffffu, v.y, off);
+        }
+        if (lane == 0) R[(size_t)ch * Nc + row] = v;
+    }
+}
+
+// ---------------------------------------------------------------- near field
+// Method 3 correction in coarse-basis form, one CTA per target dense point k:
+//   phase 1: y1(k, s) = sum h_head(q_dense) x(k', k~_s), z(k, s) = sum x(k', k~_s) over the
+//            near k' whose corner k~_s lies in slot s (lists built at set-up);
+//   phase 2: u(k, l) = sum_s Hv(k~_l, k~_s) [y1 - h_head(q_coarse) z] Hc(k~_l, k~_s)^T.
+// The prolong kernel applies F(k, k~_l) and 1/N_div.
+template <typename T>
+__global__ void __launch_bounds__(256) k_near_field(
+    const typename Cx<T>::V* __restrict__ X, const NearEntry* __restrict__ list,
+    const int* __restrict__ list_start, const T* __restrict__ hd, const typename Cx<T>::V* __restrict__ Hv,
+    const typename Cx<T>::V* __restrict__ Hc, const T* __restrict__ hc, int n, int nd, int nv, int nc,
+    int nb1, int smin, int ns1, int rmin, int nr1, int nchains, typename Cx<T>::V* __restrict__ U) {
+    using V = typename Cx<T>::V;
+    extern __shared__ unsigned char smem_raw[];
+    const int t = nv * nc;
+    const int nslot = ns1 * ns1 * ns1;
+    V* y1 = reinterpret_cast<V*>(smem_raw);
+    V* z = y1 + nslot * t;
+    const int Ndiv = nd * nd * nd;
+    const int nk = n * n * n * Ndiv;
+    const int kd = blockIdx.x;
+    const int cell = kd / Ndiv, js = kd % Ndiv;
+    const Int3 ci = unflat3(cell, n);
+    const int* st = list_start + (size_t)js * (nslot + 1);
+    for (int ch = 0; ch < nchains; ++ch) {
+        const V* Xc = X + (size_t)ch * nk * 8 * t;
+        for (int idx = threadIdx.x; idx < nslot * t; idx += blockDim.x) {
+            const int s = idx / t, e = idx % t;
+            V ya = czero<V>(), za = czero<V>();
+            for (int q = st[s]; q < st[s + 1]; ++q) {
+                const NearEntry en = list[q];
+                const int co1 = (en.co & 15) - 8, co2 = ((en.co >> 4) & 15) - 8, co3 = ((en.co >> 8) & 15) - 8;
+                const int src = flat3(ci.a + co1, ci.b + co2, ci.c + co3, n);
+                const V xv = Xc[(((size_t)src * Ndiv + en.js_src) * 8 + en.l_src) * t + e];
+                ya = cadd(ya, cscale(xv, hd[en.near_idx]));
+                za = cadd(za, xv);
+            }
+            y1[idx] = ya;
+            z[idx] = za;
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < 8 * t; idx += blockDim.x) {
+            const int l = idx / t, e = idx % t;
+            if (interp_weight(js, l, nd, nb1) == 0.0) continue;
+            const int l1 = (l >> 2) & 1, l2 = (l >> 1) & 1, l3 = l & 1;
+            const int kt = flat3(ci.a + l1, ci.b + l2, ci.c + l3, n);
+            const int n1 = e / nc, n2 = e % nc;
+            V acc = czero<V>();
+            for (int s = 0; s < nslot; ++s) {
+                const Int3 so = unflat3(s, ns1);
+                const int ra = so.a + smin - l1 - rmin, rb = so.b + smin - l2 - rmin, rc = so.c + smin - l3 - rmin;
+                const int r = (ra * nr1 + rb) * nr1 + rc;
+                const V* hv = Hv + ((size_t)kt * nr1 * nr1 * nr1 + r) * nv * nv + n1 * nv;
+                const V* hcm = Hc + ((size_t)kt * nr1 * nr1 * nr1 + r) * nc * nc + n2 * nc;
+                const T hcr = hc[r];
+                const V* ys = y1 + s * t;
+                const V* zs = z + s * t;
+                for (int n3 = 0; n3 < nv; ++n3) {
+                    V inner = czero<V>();
+                    for (int n4 = 0; n4 < nc; ++n4) {
+                        const V g = csub(ys[n3 * nc + n4], cscale(zs[n3 * nc + n4], hcr));
+                        inner = cadd(inner, cmul(g, hcm[n4]));
+                    }
+                    acc = cadd(acc, cmul(hv[n3], inner));
+                }
+            }
+            U[(((size_t)ch * nk + kd) * 8 + l) * t + e] = acc;
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------- prolong + diagonal
+// w = dE psi + (1/N_div) sum_l f Dv^T (R(k~_l) + u(k, l)) conj(Dc); one thread
+// per dense element (kd, v, c) serving all chains; block partials of <psi, w>.
+template <typename T, bool NEAR>
+__global__ void __launch_bounds__(BSE_VEC_THREADS) k_prolong(
+    const typename Cx<T>::V* __restrict__ R, const typename Cx<T>::V* __restrict__ Unf,
+    const typename Cx<T>::V* __restrict__ Dv, const typename Cx<T>::V* __restrict__ Dc,
+    const T* __restrict__ dE, const typename Cx<T>::V* __restrict__ psi, int n, int nd, int nv, int nc,
+    int nb1, int nchains, int N, int Nc, typename Cx<T>::V* __restrict__ W, double2* __restrict__ part) {
+    using V = typename Cx<T>::V;
+    __shared__ double2 red[BSE_MAX_CHAINS][BSE_VEC_THREADS];
+    const int t = nv * nc;
+    const int Ndiv = nd * nd * nd;
+    const int nk = N / t;
+    const T inv_ndiv = (T)1 / (T)Ndiv;
+    double2 dot[BSE_MAX_CHAINS];
+#pragma unroll
+    for (int ch = 0; ch < BSE_MAX_CHAINS; ++ch) dot[ch] = make_double2(0.0, 0.0);
+    for (int gid = blockIdx.x * blockDim.x + threadIdx.x; gid < N; gid += gridDim.x * blockDim.x) {
+        const int kd = gid / t, e = gid % t, v = e / nc, c = e % nc;
+        const int cell = kd / Ndiv, js = kd % Ndiv;
+        const Int3 ci = unflat3(cell, n);
+        V acc[BSE_MAX_CHAINS];
+#pragma unroll
+        for (int ch = 0; ch < BSE_MAX_CHAINS; ++ch) acc[ch] = czero<V>();
+        for (int l = 0; l < 8; ++l) {
+            const T f = (T)interp_weight(js, l, nd, nb1);
+            if (f == (T)0) continue;
+            const int cc = flat3(ci.a + ((l >> 2) & 1), ci.b + ((l >> 1) & 1), ci.c + (l & 1), n);
+            const V* dv = Dv + ((size_t)kd * 8 + l) * nv * nv;
+            const V* dc = Dc + ((size_t)kd * 8 + l) * nc * nc;
+            for (int n1 = 0; n1 < nv; ++n1) {
+                const V a = cscale(dv[n1 * nv + v], f);
+                for (int n2 = 0; n2 < nc; ++n2) {
+                    const V wgt = cmul(a, conjg(dc[n2 * nc + c]));
+                    const int q = n1 * nc + n2;
+#pragma unroll
+                    for (int ch = 0; ch < BSE_MAX_CHAINS; ++ch) {
+                        if (ch >= nchains) break;
+                        V r = R[(size_t)ch * Nc + (size_t)cc * t + q];
+                        if (NEAR) r = cadd(r, Unf[(((size_t)ch * nk + kd) * 8 + l) * t + q]);
+                        acc[ch] = cadd(acc[ch], cmul(wgt, r));
+                    }
+                }
+            }
+        }
+        const T de = dE[gid];
+#pragma unroll
+        for (int ch = 0; ch < BSE_MAX_CHAINS; ++ch) {
+            if (ch >= nchains) break;
+            const V p = psi[(size_t)ch * N + gid];
+            const V w = cadd(cscale(p, de), cscale(acc[ch], inv_ndiv));
+            W[(size_t)ch * N + gid] = w;
+            const double2 pd = to_d2(p), wd = to_d2(w);
+            dot[ch].x += pd.x * wd.x + pd.y * wd.y;
+            dot[ch].y += pd.x * wd.y - pd.y * wd.x;
+        }
+    }
+    for (int ch = 0; ch < nchains; ++ch) red[ch][threadIdx.x] = dot[ch];
+    __syncthreads();
+    for (int s = BSE_VEC_THREADS / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int ch = 0; ch < nchains; ++ch) red[ch][threadIdx.x] = cadd(red[ch][threadIdx.x], red[ch][threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x < nchains) part[(size_t)threadIdx.x * BSE_MAX_VEC_BLOCKS + blockIdx.x] = red[threadIdx.x][0];
+}
+
+// ------------------------------------------------------------- Lanczos steps
+__device__ inline double2 block_sum2(double2 v, double2* sh) {
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] = cadd(sh[threadIdx.x], sh[threadIdx.x + s]);
+        __syncthreads();
+    }
+    const double2 r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// a_i = Re sum(partials), one block per chain; the imaginary part is kept as a
+// Hermiticity diagnostic.
+__global__ void k_reduce_a(const double2* __restrict__ part, int nblk, int step, int m,
+                           double* __restrict__ a, double* __restrict__ aim, const int* __restrict__ stop) {
+    __shared__ double2 sh[256];
+    const int ch = blockIdx.x;
+    if (stop[ch]) return;
+    double2 s = make_double2(0.0, 0.0);
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) s = cadd(s, part[(size_t)ch * BSE_MAX_VEC_BLOCKS + i]);
+    s = block_sum2(s, sh);
+    if (threadIdx.x == 0) {
+        a[ch * m + step] = s.x;
+        aim[ch * m + step] = s.y;
+    }
+}
+
+// w <- w - a_i psi_i - b_i psi_{i-1}; block partials of ||w||^2.
+template <typename T>
+__global__ void __launch_bounds__(BSE_VEC_THREADS) k_lanczos_axpy(
+    typename Cx<T>::V* __restrict__ W, const typename Cx<T>::V* __restrict__ psi,
+    const typename Cx<T>::V* __restrict__ psi_prev, const double* __restrict__ a, const double* __restrict__ b,
+    int step, int m, int N, int nchains, double* __restrict__ part, const int* __restrict__ stop) {
+    using V = typename Cx<T>::V;
+    __shared__ double2 sh[BSE_VEC_THREADS];
+    for (int ch = 0; ch < nchains; ++ch) {
+        if (stop[ch]) continue;
+        const double ai = a[ch * m + step];
+        const double bi = b[ch * (m + 1) + step];
+        double nrm = 0.0;
+        for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < N; g += gridDim.x * blockDim.x) {
+            const size_t o = (size_t)ch * N + g;
+            const double2 w = to_d2(W[o]), p = to_d2(psi[o]), q = to_d2(psi_prev[o]);
+            const double2 r = make_double2(w.x - ai * p.x - bi * q.x, w.y - ai * p.y - bi * q.y);
+            const V rv = from_d2<V>(r);
+            W[o] = rv;
+            const double2 rd = to_d2(rv);
+            nrm += rd.x * rd.x + rd.y * rd.y;
+        }
+        const double2 s = block_sum2(make_double2(nrm, 0.0), sh);
+        if (threadIdx.x == 0) part[(size_t)ch * BSE_MAX_VEC_BLOCKS + blockIdx.x] = s.x;
+    }
+}
+
+// Classical Gram-Schmidt pass, part 1: partials of h_j = <V_j, w>, j = 0..nb-1.
+template <typename T>
+__global__ void __launch_bounds__(BSE_VEC_THREADS) k_cgs_dots(const typename Cx<T>::V* __restrict__ basis,
+                                                             const typename Cx<T>::V* __restrict__ W, int nb,
+                                                             int mb, int N, int ch, int nblk,
+                                                             double2* __restrict__ part) {
+    __shared__ double2 sh[BSE_VEC_THREADS];
+    const int j = blockIdx.y;
+    const auto* vj = basis + ((size_t)ch * mb + j) * N;
+    const auto* w = W + (size_t)ch * N;
+    double2 s = make_double2(0.0, 0.0);
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < N; g += gridDim.x * blockDim.x) {
+        const double2 a = to_d2(vj[g]), b = to_d2(w[g]);
+        s.x += a.x * b.x + a.y * b.y;
+        s.y += a.x * b.y - a.y * b.x;
+    }
+    s = block_sum2(s, sh);
+    if (threadIdx.x == 0) part[(size_t)j * nblk + blockIdx.x] = s;
+    (void)nb;
+}
+
+__global__ void k_cgs_reduce(const double2* __restrict__ part, int nblk, double2* __restrict__ h) {
+    __shared__ double2 sh[256];
+    const int j = blockIdx.x;
+    double2 s = make_double2(0.0, 0.0);
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) s = cadd(s, part[(size_t)j * nblk + i]);
+    s = block_sum2(s, sh);
+    if (threadIdx.x == 0) h[j] = s;
+}
+
+// Part 2: w <- w - sum_j h_j V_j; block partials of ||w||^2.
+template <typename T>
+__global__ void __launch_bounds__(BSE_VEC_THREADS) k_cgs_update(const typename Cx<T>::V* __restrict__ basis,
+                                                               typename Cx<T>::V* __restrict__ W,
+                                                               const double2* __restrict__ h, int nb, int mb,
+                                                               int N, int ch, double* __restrict__ part) {
+    using V = typename Cx<T>::V;
+    __shared__ double2 sh[BSE_VEC_THREADS];
+    double nrm = 0.0;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < N; g += gridDim.x * blockDim.x) {
+        double2 w = to_d2(W[(size_t)ch * N + g]);
+        for (int j = 0; j < nb; ++j) {
+            const double2 v = to_d2(basis[((size_t)ch * mb + j) * N + g]);
+            const double2 hj = h[j];
+            w.x -= hj.x * v.x - hj.y * v.y;
+            w.y -= hj.x * v.y + hj.y * v.x;
+        }
+        const V wv = from_d2<V>(w);
+        W[(size_t)ch * N + g] = wv;
+        const double2 wd = to_d2(wv);
+        nrm += wd.x * wd.x + wd.y * wd.y;
+    }
+    const double2 s = block_sum2(make_double2(nrm, 0.0), sh);
+    if (threadIdx.x == 0) part[(size_t)ch * BSE_MAX_VEC_BLOCKS + blockIdx.x] = s.x;
+}
+
+// b_{i+1} = sqrt(sum partials); breakdown when b_{i+1} < 1e-12 max_j |a_j|.
+__global__ void k_reduce_b(const double* __restrict__ part, int nblk, int step, int m, const double* __restrict__ a,
+                           double* __restrict__ b, int* __restrict__ stop) {
+    __shared__ double2 sh[256];
+    const int ch = blockIdx.x;
+    if (stop[ch]) return;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) s += part[(size_t)ch * BSE_MAX_VEC_BLOCKS + i];
+    const double2 r = block_sum2(make_double2(s, 0.0), sh);
+    if (threadIdx.x == 0) {
+        const double bn = sqrt(r.x);
+        b[ch * (m + 1) + step + 1] = bn;
+        double amax = 0.0;
+        for (int j = 0; j <= step; ++j) amax = fmax(amax, fabs(a[ch * m + j]));
+        if (!(bn >= 1e-12 * amax)) stop[ch] = step + 1;
+    }
+}
+
+// psi_{i+1} = w / b_{i+1} (written over psi_{i-1}), also into the basis when kept.
+template <typename T>
+__global__ void __launch_bounds__(BSE_VEC_THREADS) k_lanczos_scale(
+    const typename Cx<T>::V* __restrict__ W, typename Cx<T>::V* __restrict__ out, const double* __restrict__ b,
+    int step, int m, int N, int nchains, typename Cx<T>::V* __restrict__ basis, int mb, const int* __restrict__ stop) {
+    using V = typename Cx<T>::V;
+    for (int ch = 0; ch < nchains; ++ch) {
+        if (stop[ch]) continue;
+        const double inv = 1.0 / b[ch * (m + 1) + step + 1];
+        for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < N; g += gridDim.x * blockDim.x) {
+            const double2 w = to_d2(W[(size_t)ch * N + g]);
+            const V v = from_d2<V>(make_double2(w.x * inv, w.y * inv));
+            out[(size_t)ch * N + g] = v;
+            if (basis) basis[((size_t)ch * mb + step + 1) * N + g] = v;
+        }
+    }
+}
+
+// Start vectors: P(e) = sum_alpha e_alpha P^alpha; partial ||P||^2.
+template <typename T>
+__global__ void __launch_bounds__(BSE_VEC_THREADS) k_dipole_start(const double2* __restrict__ P, const double* __restrict__ dirs,
+                                                                  int N, int nchains, typename Cx<T>::V* __restrict__ out,
+                                                                  double* __restrict__ part) {
+    using V = typename Cx<T>::V;
+    __shared__ double2 sh[BSE_VEC_THREADS];
+    for (int ch = 0; ch < nchains; ++ch) {
+        const double e0 = dirs[3 * ch], e1 = dirs[3 * ch + 1], e2 = dirs[3 * ch + 2];
+        double nrm = 0.0;
+        for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < N; g += gridDim.x * blockDim.x) {
+            const double2 p0 = P[g], p1 = P[(size_t)N + g], p2 = P[(size_t)2 * N + g];
+            const double2 p = make_double2(e0 * p0.x + e1 * p1.x + e2 * p2.x, e0 * p0.y + e1 * p1.y + e2 * p2.y);
+            out[(size_t)ch * N + g] = from_d2<V>(p);
+            nrm += p.x * p.x + p.y * p.y;
+        }
+        const double2 s = block_sum2(make_double2(nrm, 0.0), sh);
+        if (threadIdx.x == 0) part[(size_t)ch * BSE_MAX_VEC_BLOCKS + blockIdx.x] = s.x;
+    }
+}
+
+// ||P||^2 per chain and psi_1 = P / ||P|| (in place); b_1 = 0.
+template <typename T>
+__global__ void k_start_norm(const double* __restrict__ part, int nblk, int m, double* __restrict__ pn2,
+                             double* __restrict__ b) {
+    __shared__ double2 sh[256];
+    const int ch = blockIdx.x;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) s += part[(size_t)ch * BSE_MAX_VEC_BLOCKS + i];
+    const double2 r = block_sum2(make_double2(s, 0.0), sh);
+    if (threadIdx.x == 0) {
+        pn2[ch] = r.x;
+        if (b) b[ch * (m + 1)] = 0.0;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BSE_VEC_THREADS) k_start_scale(typename Cx<T>::V* __restrict__ v, const double* __restrict__ pn2,
+                                                                 int N, int nchains, typename Cx<T>::V* __restrict__ zero_me,
+                                                                 typename Cx<T>::V* __restrict__ basis, int mb) {
+    using V = typename Cx<T>::V;
+    for (int ch = 0; ch < nchains; ++ch) {
+        const double inv = 1.0 / sqrt(pn2[ch]);
+        for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < N; g += gridDim.x * blockDim.x) {
+            const double2 p = to_d2(v[(size_t)ch * N + g]);
+            const V s = from_d2<V>(make_double2(p.x * inv, p.y * inv));
+            v[(size_t)ch * N + g] = s;
+            zero_me[(size_t)ch * N + g] = czero<V>();
+            if (basis) basis[((size_t)ch * mb) * N + g] = s;
+        }
+    }
+}
+
+// Continued fraction, one thread per (chain, omega), FP64 (Eq. fraccont).
+__global__ void k_cont_frac(const double* __restrict__ a, const double* __restrict__ b, const int* __restrict__ steps,
+                            const double* __restrict__ pn2, int m, int nchains, double pref, double eta, int nw,
+                            const double* __restrict__ omega, double2* __restrict__ eps) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nchains * nw) return;
+    const int ch = idx / nw, iw = idx % nw;
+    const int ms = steps[ch];
+    const double zr = omega[iw], zi = eta;
+    // g = 1 / (z - a_m), then g = 1 / (z - a_i - b_{i+1}^2 g)
+    double gr = 0.0, gi = 0.0;
+    for (int i = ms - 1; i >= 0; --i) {
+        const double b2 = (i == ms - 1) ? 0.0 : b[ch * (m + 1) + i + 1] * b[ch * (m + 1) + i + 1];
+        const double dr = zr - a[ch * m + i] - b2 * gr;
+        const double di = zi - b2 * gi;
+        const double den = dr * dr + di * di;
+        gr = dr / den;
+        gi = -di / den;
+    }
+    eps[idx] = make_double2(1.0 - pref * pn2[ch] * gr, -pref * pn2[ch] * gi);
+}
+
+inline int vec_blocks(long long N) {
+    long long b = (N + BSE_VEC_THREADS - 1) / BSE_VEC_THREADS;
+    return (int)std::min<long long>(std::max<long long>(b, 1), BSE_MAX_VEC_BLOCKS);
+}
+
+struct Timer {
+    bse_ctx* ctx;
+    bool on;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int cls;
+    Timer(bse_ctx* c, bool enabled, int k) : ctx(c), on(enabled), cls(k) {
+        if (on) {
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            cudaEventRecord(e0, ctx->stream);
+        }
+    }
+    ~Timer() {
+        if (on) {
+            cudaEventRecord(e1, ctx->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ctx->kt_ms[cls] += ms;
+            ctx->kt_n[cls] += 1;
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+        }
+    }
+};
+
+// One application of H to nchains vectors psi -> w (device, vector precision),
+// block partials of <psi, w> into s->d_part_dot.
+template <typename T>
+int apply_h_typed(bse_ctx* ctx, bse_interp* s, int nchains, const void* psi_v, void* w_v, bool prof) {
+    using V = typename Cx<T>::V;
+    const bse_coarse* c = s->co;
+    cudaStream_t st = ctx->stream;
+    const V* psi = (const V*)psi_v;
+    V* W = (V*)w_v;
+    const bool m3 = s->scheme == BSE_SCHEME_M3;
+    V* X = m3 ? (V*)s->d_X : nullptr;
+    {
+        Timer tm(ctx, prof, KC_RESTRICT);
+        if (c->kc_prec == BSE_PREC_BF16)
+            k_restrict<T, true><<<c->nkc, 256, 0, st>>>(psi, (const V*)s->d_Dv, (const V*)s->d_Dc, s->n, s->nd, s->nv, s->nc,
+                                                       s->nb1, nchains, s->N, c->Nc, nullptr, s->d_Bop, c->ldk, X, s->d_stop);
+        else
+            k_restrict<T, false><<<c->nkc, 256, 0, st>>>(psi, (const V*)s->d_Dv, (const V*)s->d_Dc, s->n, s->nd, s->nv, s->nc,
+                                                        s->nb1, nchains, s->N, c->Nc, (V*)s->d_Q, nullptr, 0, X, s->d_stop);
+    }
+    {
+        Timer tm(ctx, prof, KC_KCAPPLY);
+        if (c->kc_prec == BSE_PREC_BF16) {
+            int rc = bse_tc_apply(ctx, s, nchains);
+            if (rc != BSE_OK) return rc;
+        } else {
+            k_kc_apply_simt<T><<<(c->Nc + 7) / 8, 256, 0, st>>>((const V*)c->d_kc, (const V*)s->d_Q, c->Nc, nchains, (V*)s->d_R);
+        }
+    }
+    if (m3) {
+        Timer tm(ctx, prof, KC_NEAR);
+        const size_t smem = sizeof(V) * 2 * s->nslot * s->t;
+        if (smem > 48 * 1024) {
+            BSE_CUDA_TRY(ctx, cudaFuncSetAttribute(k_near_field<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        }
+        k_near_field<T><<<s->nk, 256, smem, st>>>(X, s->d_list, s->d_list_start, (const T*)s->d_hd, (const V*)s->d_Hv,
+                                                 (const V*)s->d_Hc, (const T*)s->d_hc, s->n, s->nd, s->nv, s->nc, s->nb1,
+                                                 s->smin, s->ns1, s->rmin, s->nr1, nchains, (V*)s->d_U);
+    }
+    {
+        Timer tm(ctx, prof, KC_PROLONG);
+        const int nb = vec_blocks(s->N);
+        if (m3)
+            k_prolong<T, true><<<nb, BSE_VEC_THREADS, 0, st>>>((const V*)s->d_R, (const V*)s->d_U, (const V*)s->d_Dv,
+                                                              (const V*)s->d_Dc, (const T*)s->d_dE, psi, s->n, s->nd, s->nv,
+                                                              s->nc, s->nb1, nchains, s->N, c->Nc, W, s->d_part_dot);
+        else
+            k_prolong<T, false><<<nb, BSE_VEC_THREADS, 0, st>>>((const V*)s->d_R, nullptr, (const V*)s->d_Dv,
+                                                               (const V*)s->d_Dc, (const T*)s->d_dE, psi, s->n, s->nd, s->nv,
+                                                               s->nc, s->nb1, nchains, s->N, c->Nc, W, s->d_part_dot);
+    }
+    return BSE_OK;
+}
+
+template <typename T>
+int ensure_state(bse_ctx* ctx, bse_interp* s, int m, bool reorth) {
+    using V = typename Cx<T>::V;
+    if (s->m_alloc < m) {
+        cudaFree(s->d_a); cudaFree(s->d_aim); cudaFree(s->d_b);
+        s->d_a = s->d_aim = s->d_b = nullptr;
+        s->m_alloc = 0;
+        int rc;
+        if ((rc = bse_alloc(ctx, (void**)&s->d_a, sizeof(double) * BSE_MAX_CHAINS * m, "a")) != BSE_OK) return rc;
+        if ((rc = bse_alloc(ctx, (void**)&s->d_aim, sizeof(double) * BSE_MAX_CHAINS * m, "a imag")) != BSE_OK) return rc;
+        if ((rc = bse_alloc(ctx, (void**)&s->d_b, sizeof(double) * BSE_MAX_CHAINS * (m + 1), "b")) != BSE_OK) return rc;
+        s->m_alloc = m;
+    }
+    if (reorth && s->basis_m < m + 1) {
+        cudaFree(s->d_basis); cudaFree(s->d_cgs_part); cudaFree(s->d_cgs_h);
+        s->d_basis = nullptr; s->d_cgs_part = s->d_cgs_h = nullptr;
+        s->basis_m = 0;
+        int rc;
+        if ((rc = bse_alloc(ctx, &s->d_basis, sizeof(V) * BSE_MAX_CHAINS * (size_t)(m + 1) * s->N, "Lanczos basis")) != BSE_OK) return rc;
+        if ((rc = bse_alloc(ctx, (void**)&s->d_cgs_part, sizeof(double2) * (size_t)(m + 1) * BSE_MAX_VEC_BLOCKS, "CGS partials")) != BSE_OK) return rc;
+        if ((rc = bse_alloc(ctx, (void**)&s->d_cgs_h, sizeof(double2) * (size_t)(m + 1), "CGS coefficients")) != BSE_OK) return rc;
+        s->basis_m = m + 1;
+    }
+    return BSE_OK;
+}
+
+// Enqueue the whole Haydock loop for one system on ctx->stream.
+template <typename T>
+int enqueue_chains(bse_ctx* ctx, bse_interp* s, int nch, const double* d_dirs, double* d_pn2, int m, bool reorth, bool prof) {
+    using V = typename Cx<T>::V;
+    cudaStream_t st = ctx->stream;
+    const int N = s->N;
+    const int nb = vec_blocks(N);
+    V* A = (V*)s->d_vec[0];
+    V* B = (V*)s->d_vec[1];
+    V* W = (V*)s->d_vec[2];
+    V* basis = reorth ? (V*)s->d_basis : nullptr;
+    const int mb = s->basis_m;
+    cudaMemsetAsync(s->d_stop, 0, sizeof(int) * BSE_MAX_CHAINS, st);
+    // psi_1 = P / ||P|| in B, psi_0 = 0 in A
+    k_dipole_start<T><<<nb, BSE_VEC_THREADS, 0, st>>>(s->d_P, d_dirs, N, nch, B, s->d_part_nrm);
+    k_start_norm<T><<<nch, 256, 0, st>>>(s->d_part_nrm, nb, m, d_pn2, s->d_b);
+    k_start_scale<T><<<nb, BSE_VEC_THREADS, 0, st>>>(B, d_pn2, N, nch, A, basis, mb);
+    for (int i = 0; i < m; ++i) {
+        int rc = apply_h_typed<T>(ctx, s, nch, B, W, prof);
+        if (rc != BSE_OK) return rc;
+        Timer tm(ctx, prof, KC_LANCZOS);
+        k_reduce_a<<<nch, 256, 0, st>>>(s->d_part_dot, nb, i, m, s->d_a, s->d_aim, s->d_stop);
+        k_lanczos_axpy<T><<<nb, BSE_VEC_THREADS, 0, st>>>(W, B, A, s->d_a, s->d_b, i, m, N, nch, s->d_part_nrm, s->d_stop);
+        if (reorth) {
+            for (int ch = 0; ch < nch; ++ch)
+                for (int pass = 0; pass < 2; ++pass) {
+                    dim3 g(nb, i + 1);
+                    k_cgs_dots<T><<<g, BSE_VEC_THREADS, 0, st>>>(basis, W, i + 1, mb, N, ch, nb, s->d_cgs_part);
+                    k_cgs_reduce<<<i + 1, 256, 0, st>>>(s->d_cgs_part, nb, s->d_cgs_h);
+                    k_cgs_update<T><<<nb, BSE_VEC_THREADS, 0, st>>>(basis, W, s->d_cgs_h, i + 1, mb, N, ch, s->d_part_nrm);
+                }
+        }
+        k_reduce_b<<<nch, 256, 0, st>>>(s->d_part_nrm, nb, i, m, s->d_a, s->d_b, s->d_stop);
+        k_lanczos_scale<T><<<nb, BSE_VEC_THREADS, 0, st>>>(W, A, s->d_b, i, m, N, nch, basis, mb, s->d_stop);
+        std::swap(A, B);
+    }
+    return BSE_OK;
+}
+
+template <typename T>
+int run_chains_typed(bse_ctx* ctx, bse_interp* s, int nch, const double* pol_dirs, int m, int flags, double* a,
+                     double* b, double* pnorm2, int* steps_done) {
+    const bool reorth = flags & BSE_REORTH_CGS2;
+    const bool prof = flags & BSE_PROFILE;
+    const bool graph = (flags & BSE_USE_GRAPH) && !prof;
+    int rc = ensure_state<T>(ctx, s, m, reorth);
+    if (rc != BSE_OK) return rc;
+    cudaStream_t st = ctx->stream;
+    double* d_dirs = nullptr;
+    double* d_pn2 = nullptr;
+    // small per-run buffers live in the handle's Q scratch tail? keep them separate and explicit
+    if ((rc = bse_alloc(ctx, (void**)&d_dirs, sizeof(double) * 3 * BSE_MAX_CHAINS, "directions")) != BSE_OK) return rc;
+    if ((rc = bse_alloc(ctx, (void**)&d_pn2, sizeof(double) * BSE_MAX_CHAINS, "norms")) != BSE_OK) { cudaFree(d_dirs); return rc; }
+    BSE_CUDA_TRY(ctx, cudaMemcpyAsync(d_dirs, pol_dirs, sizeof(double) * 3 * nch, cudaMemcpyHostToDevice, st));
+    if (prof) for (int k = 0; k < KC_COUNT; ++k) { ctx->kt_ms[k] = 0; ctx->kt_n[k] = 0; }
+    if (graph) {
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ge = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            rc = enqueue_chains<T>(ctx, s, nch, d_dirs, d_pn2, m, reorth, false);
+            e = cudaStreamEndCapture(st, &g);
+        }
+        if (e == cudaSuccess && rc == BSE_OK) e = cudaGraphInstantiate(&ge, g, 0);
+        if (e == cudaSuccess && rc == BSE_OK) e = cudaGraphLaunch(ge, st);
+        if (ge) cudaGraphExecDestroy(ge);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            cudaFree(d_dirs); cudaFree(d_pn2);
+            ctx->err = std::string("graph capture/launch: ") + cudaGetErrorString(e);
+            return BSE_ERR_CUDA;
+        }
+    } else {
+        rc = enqueue_chains<T>(ctx, s, nch, d_dirs, d_pn2, m, reorth, prof);
+    }
+    if (rc != BSE_OK) { cudaFree(d_dirs); cudaFree(d_pn2); return rc; }
+    std::vector<int> stop(BSE_MAX_CHAINS);
+    int status = 0;
+    cudaMemcpyAsync(pnorm2, d_pn2, sizeof(double) * nch, cudaMemcpyDeviceToHost, st);
+    for (int ch = 0; ch < nch; ++ch) {
+        cudaMemcpyAsync(a + (size_t)ch * m, s->d_a + (size_t)ch * m, sizeof(double) * m, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(b + (size_t)ch * (m + 1), s->d_b + (size_t)ch * (m + 1), sizeof(double) * (m + 1), cudaMemcpyDeviceToHost, st);
+    }
+    cudaMemcpyAsync(stop.data(), s->d_stop, sizeof(int) * BSE_MAX_CHAINS, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    cudaFree(d_dirs);
+    cudaFree(d_pn2);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        ctx->err = std::string("Haydock run: ") + cudaGetErrorString(e);
+        return BSE_ERR_CUDA;
+    }
+    if (status != 0) {
+        ctx->err = "a bounded device wait in the tensor-core K_c apply gave up";
+        cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st);
+        return BSE_ERR_TIMEOUT;
+    }
+    int warn = BSE_OK;
+    for (int ch = 0; ch < nch; ++ch) {
+        steps_done[ch] = stop[ch] ? stop[ch] : m;
+        if (stop[ch]) warn = BSE_WARN_BREAKDOWN;
+    }
+    return warn;
+}
+
+template <typename T>
+int dipoles_typed(bse_ctx* ctx, bse_interp* s, int npol, const double* pol_dirs, void* p_out, double* pnorm2) {
+    cudaStream_t st = ctx->stream;
+    double* d_dirs = nullptr;
+    double* d_pn2 = nullptr;
+    int rc;
+    if ((rc = bse_alloc(ctx, (void**)&d_dirs, sizeof(double) * 3 * BSE_MAX_CHAINS, "directions")) != BSE_OK) return rc;
+    if ((rc = bse_alloc(ctx, (void**)&d_pn2, sizeof(double) * BSE_MAX_CHAINS, "norms")) != BSE_OK) { cudaFree(d_dirs); return rc; }
+    cudaMemcpyAsync(d_dirs, pol_dirs, sizeof(double) * 3 * npol, cudaMemcpyHostToDevice, st);
+    const int nb = vec_blocks(s->N);
+    k_dipole_start<T><<<nb, BSE_VEC_THREADS, 0, st>>>(s->d_P, d_dirs, s->N, npol, (typename Cx<T>::V*)p_out, s->d_part_nrm);
+    k_start_norm<T><<<npol, 256, 0, st>>>(s->d_part_nrm, nb, 0, d_pn2, nullptr);
+    cudaMemcpyAsync(pnorm2, d_pn2, sizeof(double) * npol, cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    cudaFree(d_dirs);
+    cudaFree(d_pn2);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) { ctx->err = std::string("dipoles: ") + cudaGetErrorString(e); return BSE_ERR_CUDA; }
+    return BSE_OK;
+}
+
+}  // namespace
+
+int bse_apply_once(bse_ctx* ctx, bse_interp* s, int nvec, const void* x, void* y, bool profile) {
+    int rc = (s->vec_prec == BSE_PREC_F64) ? apply_h_typed<double>(ctx, s, nvec, x, y, profile)
+                                           : apply_h_typed<float>(ctx, s, nvec, x, y, profile);
+    if (rc != BSE_OK) return rc;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) { ctx->err = std::string("apply H: ") + cudaGetErrorString(e); return BSE_ERR_CUDA; }
+    int status = 0;
+    cudaMemcpy(&status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (status) {
+        cudaMemset(ctx->d_status, 0, sizeof(int));
+        ctx->err = "a bounded device wait in the tensor-core K_c apply gave up";
+        return BSE_ERR_TIMEOUT;
+    }
+    return BSE_OK;
+}
+
+int bse_run_chains(bse_ctx* ctx, bse_interp* s, int npol, const double* pol_dirs, int nsteps, int flags, double* a,
+                   double* b, double* pnorm2, int* steps_done) {
+    if (s->vec_prec == BSE_PREC_F64)
+        return run_chains_typed<double>(ctx, s, npol, pol_dirs, nsteps, flags, a, b, pnorm2, steps_done);
+    return run_chains_typed<float>(ctx, s, npol, pol_dirs, nsteps, flags, a, b, pnorm2, steps_done);
+}
+
+int bse_make_dipoles(bse_ctx* ctx, bse_interp* s, int npol, const double* pol_dirs, void* p_out, double* pnorm2) {
+    if (s->vec_prec == BSE_PREC_F64) return dipoles_typed<double>(ctx, s, npol, pol_dirs, p_out, pnorm2);
+    return dipoles_typed<float>(ctx, s, npol, pol_dirs, p_out, pnorm2);
+}
+
+int bse_cf_device(bse_ctx* ctx, int nchains, int nsteps, const int* steps_done, const double* a, const double* b,
+                  const double* pnorm2, double prefactor, double eta, int nw, const double* omega, double* eps) {
+    cudaStream_t st = ctx->stream;
+    double *d_a = nullptr, *d_b = nullptr, *d_pn = nullptr, *d_w = nullptr;
+    int* d_s = nullptr;
+    double2* d_eps = nullptr;
+    int rc = BSE_OK;
+    if ((rc = bse_alloc(ctx, (void**)&d_a, sizeof(double) * nchains * nsteps, "a")) != BSE_OK) return rc;
+    if ((rc = bse_alloc(ctx, (void**)&d_b, sizeof(double) * nchains * (nsteps + 1), "b")) != BSE_OK) goto out;
+    if ((rc = bse_alloc(ctx, (void**)&d_pn, sizeof(double) * nchains, "pnorm2")) != BSE_OK) goto out;
+    if ((rc = bse_alloc(ctx, (void**)&d_w, sizeof(double) * nw, "omega")) != BSE_OK) goto out;
+    if ((rc = bse_alloc(ctx, (void**)&d_s, sizeof(int) * nchains, "steps")) != BSE_OK) goto out;
+    if ((rc = bse_alloc(ctx, (void**)&d_eps, sizeof(double2) * nchains * nw, "eps")) != BSE_OK) goto out;
+    cudaMemcpyAsync(d_a, a, sizeof(double) * nchains * nsteps, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(d_b, b, sizeof(double) * nchains * (nsteps + 1), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(d_pn, pnorm2, sizeof(double) * nchains, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(d_w, omega, sizeof(double) * nw, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(d_s, steps_done, sizeof(int) * nchains, cudaMemcpyHostToDevice, st);
+    k_cont_frac<<<(nchains * nw + 127) / 128, 128, 0, st>>>(d_a, d_b, d_s, d_pn, nsteps, nchains, prefactor, eta, nw, d_w, d_eps);
+    cudaMemcpyAsync(eps, d_eps, sizeof(double2) * nchains * nw, cudaMemcpyDeviceToHost, st);
+    {
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e != cudaSuccess) { ctx->err = std::string("continued fraction: ") + cudaGetErrorString(e); rc = BSE_ERR_CUDA; }
+    }
+out:
+    cudaFree(d_a); cudaFree(d_b); cudaFree(d_pn); cudaFree(d_w); cudaFree(d_s); cudaFree(d_eps);
+    return rc;
+}

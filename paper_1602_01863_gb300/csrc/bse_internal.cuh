@@ -1,0 +1,196 @@
+// Internal declarations of the GB300 double-grid BSE Haydock library.
+//
+// Data layout on the device (all row-major, complex interleaved):
+//   coarse  Uv [nkc][nv][nv], Uc [nkc][nc][nc]      band gauge at coarse points (FP64)
+//           K_c: complex128 / complex64 [Nc][Nc], or BF16 planes Kr, Ki [Nc][ldk]
+//   dense   dE [N] (vector precision), P^alpha [3][N] (FP64)
+//           Dv [nk][8][nv][nv], Dc [nk][8][nc][nc]  overlaps d per corner (Eq. completeness)
+//   M3      near-pair contribution lists per sub-cell position, head factors
+//           Hv [nkc][nrel][nv][nv] = alpha O^v, Hc [nkc][nrel][nc][nc] = O^c, hc [nrel]
+//   vectors [chain][N]; coarse vectors [chain][Nc]; per-(dense k, corner)
+//           restricted pieces X and near-field results Unf [chain][nk][8][t].
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "bse.h"
+
+#define BSE_MAX_BANDS 8
+#define BSE_MAX_T (BSE_MAX_BANDS * BSE_MAX_BANDS)
+#define BSE_MAX_CHAINS 4
+#define BSE_VEC_THREADS 256
+#define BSE_MAX_VEC_BLOCKS 1024
+
+// ------------------------------------------------------------ complex math
+__host__ __device__ inline double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ inline float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// conj(a) * b
+__host__ __device__ inline double2 cmulc(double2 a, double2 b) {
+    return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__host__ __device__ inline float2 cmulc(float2 a, float2 b) {
+    return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__host__ __device__ inline double2 conjg(double2 a) { return make_double2(a.x, -a.y); }
+__host__ __device__ inline float2 conjg(float2 a) { return make_float2(a.x, -a.y); }
+__host__ __device__ inline double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__host__ __device__ inline float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
+template <typename T> struct Cx;
+template <> struct Cx<double> { using V = double2; };
+template <> struct Cx<float> { using V = float2; };
+
+template <typename V> __host__ __device__ inline V czero();
+template <> __host__ __device__ inline double2 czero<double2>() { return make_double2(0.0, 0.0); }
+template <> __host__ __device__ inline float2 czero<float2>() { return make_float2(0.f, 0.f); }
+
+template <typename V> __host__ __device__ inline V from_d2(double2 a);
+template <> __host__ __device__ inline double2 from_d2<double2>(double2 a) { return a; }
+template <> __host__ __device__ inline float2 from_d2<float2>(double2 a) {
+    return make_float2((float)a.x, (float)a.y);
+}
+__host__ __device__ inline double2 to_d2(double2 a) { return a; }
+__host__ __device__ inline double2 to_d2(float2 a) { return make_double2(a.x, a.y); }
+
+// --------------------------------------------------------- grid utilities
+struct Int3 { int a, b, c; };
+
+__host__ __device__ inline int imod(int a, int n) { int r = a % n; return r < 0 ? r + n : r; }
+__host__ __device__ inline int floordiv(int a, int n) { return (a - imod(a, n)) / n; }
+__host__ __device__ inline Int3 unflat3(int idx, int n) { return Int3{idx / (n * n), (idx / n) % n, idx % n}; }
+__host__ __device__ inline int flat3(int a, int b, int c, int n) {
+    return (imod(a, n) * n + imod(b, n)) * n + imod(c, n);
+}
+
+// Interpolation prefactor f(k, k~^{lmn}) for sub-cell position js and corner l
+// (l = l1*4 + l2*2 + l3): trilinear f^l_j = (1 - j/n_div | j/n_div) per axis
+// (Sec. 3, Eq. interpwfn), or the one-neighbour scheme (Eq. eqRL: f = 1 on
+// the nearest corner, j/n_div = 1/2 going to l = 0).
+__host__ __device__ inline double interp_weight(int js, int l, int nd, int nb1) {
+    const int j1 = js / (nd * nd), j2 = (js / nd) % nd, j3 = js % nd;
+    const int l1 = (l >> 2) & 1, l2 = (l >> 1) & 1, l3 = l & 1;
+    if (nb1) {
+        return ((2 * j1 > nd) == l1 && (2 * j2 > nd) == l2 && (2 * j3 > nd) == l3) ? 1.0 : 0.0;
+    }
+    const double f1 = l1 ? (double)j1 / nd : 1.0 - (double)j1 / nd;
+    const double f2 = l2 ? (double)j2 / nd : 1.0 - (double)j2 / nd;
+    const double f3 = l3 ? (double)j3 / nd : 1.0 - (double)j3 / nd;
+    return f1 * f2 * f3;
+}
+
+// ------------------------------------------------------------------ handles
+enum KernelClass { KC_RESTRICT = 0, KC_KCAPPLY = 1, KC_PROLONG = 2, KC_NEAR = 3, KC_LANCZOS = 4, KC_COUNT = 5 };
+
+struct bse_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;          // created by the context (caller passed NULL)
+    std::string err;
+    int* d_status = nullptr;          // device status word: bit 0 = bounded wait gave up
+    double kt_ms[KC_COUNT] = {0, 0, 0, 0, 0};
+    long long kt_n[KC_COUNT] = {0, 0, 0, 0, 0};
+    int sm_count = 0;
+};
+
+struct bse_coarse {
+    int n = 0, nv = 0, nc = 0, t = 0, nkc = 0, Nc = 0;
+    int kc_prec = 0, ldk = 0;
+    double eps_inf = 0, kappa = 0, e_k = 0, e_gap = 0, band_width = 0, h0 = 0, alpha = 0;
+    int direct_shells = 27, h_const = 0, exchange_on = 1;
+    // model parameters on the device (FP64)
+    double* d_offsets = nullptr;
+    double2 *d_gen_v = nullptr, *d_gen_c = nullptr, *d_mu = nullptr, *d_dip = nullptr;
+    double2 *d_Uv = nullptr, *d_Uc = nullptr;     // coarse band gauge
+    void* d_kc = nullptr;                         // K_c storage
+    __nv_bfloat16 *d_kr = nullptr, *d_ki = nullptr; // BF16 planes (inside d_kc)
+};
+
+struct NearEntry { int co; int js_src; int l_src; int near_idx; };   // co packed 3 x 4 bits (+8 bias)
+
+struct bse_interp {
+    const bse_coarse* co = nullptr;
+    int n = 0, nd = 0, Ndiv = 0, nk = 0, N = 0, t = 0, nv = 0, nc = 0;
+    int scheme = 0, nb1 = 0, vec_prec = 0;
+    double width = 0;
+    // dense tables
+    void* d_dE = nullptr;            // T [N]
+    void* d_Dv = nullptr;            // V [nk][8][nv*nv]
+    void* d_Dc = nullptr;            // V [nk][8][nc*nc]
+    double2* d_P = nullptr;          // [3][N]
+    // M3 tables
+    int n_near = 0, smin = 0, ns1 = 0, nslot = 0, rmin = 0, nr1 = 0, nrel = 0;
+    NearEntry* d_list = nullptr;
+    int* d_list_start = nullptr;     // [Ndiv][nslot + 1]
+    void* d_hd = nullptr;            // T [n_near]   h_head at dense near offsets
+    void* d_Hv = nullptr;            // V [nkc][nrel][nv*nv]
+    void* d_Hc = nullptr;            // V [nkc][nrel][nc*nc]
+    void* d_hc = nullptr;            // T [nrel]
+    // scratch (BSE_MAX_CHAINS chains)
+    void* d_Q = nullptr;             // V [4][Nc]  restricted coarse vectors
+    void* d_R = nullptr;             // V [4][Nc]  K_c Q
+    void* d_X = nullptr;             // V [4][nk][8][t]
+    void* d_U = nullptr;             // V [4][nk][8][t]
+    __nv_bfloat16* d_Bop = nullptr;  // [16][ldk] split-BF16 operand of the tensor-core apply
+    float* d_part = nullptr;         // split-K partial sums of the tensor-core apply
+    int tc_ctas = 0, tc_kblocks = 0; // tensor-core schedule
+    void* tc_state = nullptr;        // tensor maps + schedule tables (bse_tc.cu)
+    void* d_vec[3] = {nullptr, nullptr, nullptr};   // V [4][N]: psi_A, psi_B, w
+    double2* d_part_dot = nullptr;   // [4][BSE_MAX_VEC_BLOCKS] FP64 block partials
+    double* d_part_nrm = nullptr;    // [4][BSE_MAX_VEC_BLOCKS]
+    // Haydock state (device)
+    double* d_a = nullptr;           // [4][m]
+    double* d_aim = nullptr;         // [4][m]
+    double* d_b = nullptr;           // [4][m + 1]
+    int* d_stop = nullptr;           // [4]  0 = running, else steps done
+    int m_alloc = 0;
+    void* d_basis = nullptr;         // V [4][m + 1][N] when reorthogonalising
+    int basis_m = 0;
+    double2* d_cgs_part = nullptr;   // [4][(m+1)][nblk]
+    double2* d_cgs_h = nullptr;      // [4][m + 1]
+    // cached graph
+    cudaGraphExec_t graph = nullptr;
+    int graph_key[4] = {0, 0, 0, 0};
+};
+
+// ----------------------------------------------------------------- helpers
+#define BSE_CUDA_TRY(ctx, call)                                                       \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess) {                                                      \
+            (ctx)->err = std::string(#call) + ": " + cudaGetErrorString(e_);          \
+            return BSE_ERR_CUDA;                                                      \
+        }                                                                             \
+    } while (0)
+
+int bse_alloc(bse_ctx* ctx, void** p, size_t bytes, const char* what);
+
+// setup kernels (bse_setup.cu)
+int bse_setup_coarse_device(bse_ctx* ctx, bse_coarse* c);
+int bse_setup_interp_device(bse_ctx* ctx, bse_interp* s);
+
+// hot path (bse_apply.cu)
+int bse_apply_once(bse_ctx* ctx, bse_interp* s, int nvec, const void* x, void* y, bool profile);
+int bse_run_chains(bse_ctx* ctx, bse_interp* s, int npol, const double* pol_dirs, int nsteps,
+                   int flags, double* a, double* b, double* pnorm2, int* steps_done);
+int bse_make_dipoles(bse_ctx* ctx, bse_interp* s, int npol, const double* pol_dirs, void* p_out,
+                     double* pnorm2);
+int bse_cf_device(bse_ctx* ctx, int nchains, int nsteps, const int* steps_done, const double* a,
+                  const double* b, const double* pnorm2, double prefactor, double eta, int nw,
+                  const double* omega, double* eps);
+
+// tensor-core K_c apply (bse_tc.cu)
+int bse_tc_prepare(bse_ctx* ctx, bse_interp* s);
+int bse_tc_apply(bse_ctx* ctx, bse_interp* s, int nchains);
+void bse_tc_release(bse_interp* s);
