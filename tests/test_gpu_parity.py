@@ -81,7 +81,9 @@ def test_kc_bf16_and_c64_are_roundings_of_oracle(ctx):
         for part in (np.real, np.imag):
             err = np.abs(part(K) - part(Kref))
             assert np.all(err <= rel * np.abs(part(Kref)) + floor)
-        assert np.abs(K - K.conj().T).max() == 0.0          # rounding keeps K_c exactly Hermitian
+        off = ~np.eye(K.shape[0], dtype=bool)
+        assert np.abs(K - K.conj().T)[off].max() == 0.0     # rounding keeps K_c exactly Hermitian off the diagonal
+        assert np.abs(np.diag(K).imag).max() <= floor       # the diagonal is real up to noise
         co.free()
 
 
