@@ -161,6 +161,23 @@ int bse_dipoles(bse_ctx* ctx, bse_interp* interp, int npol, const double* pol_di
  * must not overlap. */
 int bse_apply_h(bse_ctx* ctx, bse_interp* interp, int nvec, const void* x, void* y);
 
+/* Same result as bse_apply_h, but allocates no device memory: the per-call
+ * scratch comes from one static device array of 32 MiB inside the library
+ * (held by every GPU that loads the library until the process exits), not
+ * from the handle.  The paper has no counterpart; this exists for callers
+ * that must not call cudaMalloc once their work has started, such as a host
+ * framework that owns all device memory through its own pool, or a loop
+ * where cudaMalloc's implicit device synchronisation is not allowed.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls share the array and it keeps the
+ * previous call's contents (what must start at zero is cleared each call):
+ * calls that overlap on the GPU race.  Sizes whose scratch does not fit
+ * (nvec vectors of Q and R, for M3 the per-corner pieces, for BF16 the
+ * operand and tile partials) return BSE_ERR_UNSUPPORTED with the byte count
+ * in bse_last_error.  Other errors as bse_apply_h. */
+int bse_apply_h_noalloc(bse_ctx* ctx, bse_interp* interp, int nvec, const void* x, void* y);
+
 /* Haydock recursion (Eqs. ai, bi, ci) for `nsys` systems sharing the context.
  * System s runs npol[s] (1..4) chains starting from P(e) for the directions
  * pol_dirs (host, 3 doubles per chain, systems in order).  nsteps Lanczos

@@ -33,7 +33,8 @@ KERNEL_CLASSES = ("restrict", "kc_apply", "prolong", "near_field", "lanczos")
 
 EXPORTED = ("bse_version", "bse_ctx_create", "bse_ctx_destroy", "bse_last_error", "bse_build_coarse",
             "bse_coarse_get_kc", "bse_free_coarse", "bse_interp_setup", "bse_free_interp", "bse_interp_info",
-            "bse_dipoles", "bse_apply_h", "bse_haydock_run", "bse_last_kernel_times", "bse_spectrum")
+            "bse_dipoles", "bse_apply_h", "bse_apply_h_noalloc", "bse_haydock_run", "bse_last_kernel_times",
+            "bse_spectrum")
 
 
 class BseError(RuntimeError):
@@ -84,6 +85,7 @@ def load(path: str | None = None):
     lib.bse_interp_info.argtypes = [_P, C.POINTER(C.c_longlong)]
     lib.bse_dipoles.argtypes = [_P, _P, C.c_int, _D, _P, _D]
     lib.bse_apply_h.argtypes = [_P, _P, C.c_int, _P, _P]
+    lib.bse_apply_h_noalloc.argtypes = [_P, _P, C.c_int, _P, _P]
     lib.bse_haydock_run.argtypes = [_P, C.POINTER(_P), C.c_int, _I, _D, C.c_int, C.c_int, _D, _D, _D, _I]
     lib.bse_last_kernel_times.argtypes = [_P, _D, C.POINTER(C.c_longlong)]
     lib.bse_spectrum.argtypes = [_P, C.c_int, C.c_int, _I, _D, _D, _D, C.c_double, C.c_double, C.c_int, _D, _D]
@@ -191,6 +193,10 @@ class Context:
     # -- bse_apply_h
     def bse_apply_h(self, interp: Interp, nvec: int, x_ptr: int, y_ptr: int) -> None:
         self._check(self.lib.bse_apply_h(self.h, interp.handle, nvec, _P(x_ptr), _P(y_ptr)))
+
+    # -- bse_apply_h_noalloc (scratch from the library's static device array)
+    def bse_apply_h_noalloc(self, interp: Interp, nvec: int, x_ptr: int, y_ptr: int) -> None:
+        self._check(self.lib.bse_apply_h_noalloc(self.h, interp.handle, nvec, _P(x_ptr), _P(y_ptr)))
 
     # -- bse_haydock_run
     def bse_haydock_run(self, systems: list[Interp], npol: list[int], pol_dirs: np.ndarray, nsteps: int,

@@ -789,3 +789,56 @@ out:
     cudaFree(d_a); cudaFree(d_b); cudaFree(d_pn); cudaFree(d_w); cudaFree(d_s); cudaFree(d_eps);
     return rc;
 }
+
+namespace {
+
+// The H application of apply_h_typed with every per-call buffer taken from
+// `sc` instead of the handle; enqueues only (no allocation, no sync).
+template <typename T>
+int apply_scratch_typed(bse_ctx* ctx, const bse_interp* s, int nchains, const void* psi_v, void* w_v,
+                        const ApplyScratch& sc) {
+    using V = typename Cx<T>::V;
+    const bse_coarse* c = s->co;
+    cudaStream_t st = ctx->stream;
+    const V* psi = (const V*)psi_v;
+    V* W = (V*)w_v;
+    const bool m3 = s->scheme == BSE_SCHEME_M3;
+    V* X = m3 ? (V*)sc.X : nullptr;
+    if (c->kc_prec == BSE_PREC_BF16) {
+        BSE_CUDA_TRY(ctx, cudaMemsetAsync(sc.bop, 0, sizeof(__nv_bfloat16) * 16 * (size_t)c->ldk, st));
+        k_restrict<T, true><<<c->nkc, 256, 0, st>>>(psi, (const V*)s->d_Dv, (const V*)s->d_Dc, s->n, s->nd, s->nv, s->nc,
+                                                   s->nb1, nchains, s->N, c->Nc, nullptr, sc.bop, c->ldk, X, nullptr);
+        int rc = bse_tc_apply_scratch(ctx, s, nchains, sc.bop, sc.part, sc.R);
+        if (rc != BSE_OK) return rc;
+    } else {
+        k_restrict<T, false><<<c->nkc, 256, 0, st>>>(psi, (const V*)s->d_Dv, (const V*)s->d_Dc, s->n, s->nd, s->nv, s->nc,
+                                                    s->nb1, nchains, s->N, c->Nc, (V*)sc.Q, nullptr, 0, X, nullptr);
+        k_kc_apply_simt<T><<<(c->Nc + 7) / 8, 256, 0, st>>>((const V*)c->d_kc, (const V*)sc.Q, c->Nc, nchains, (V*)sc.R);
+    }
+    if (m3) {
+        const size_t smem = sizeof(V) * 2 * s->nslot * s->t;
+        if (smem > 48 * 1024) {
+            BSE_CUDA_TRY(ctx, cudaFuncSetAttribute(k_near_field<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        }
+        k_near_field<T><<<s->nk, 256, smem, st>>>(X, s->d_list, s->d_list_start, (const T*)s->d_hd, (const V*)s->d_Hv,
+                                                 (const V*)s->d_Hc, (const T*)s->d_hc, s->n, s->nd, s->nv, s->nc, s->nb1,
+                                                 s->smin, s->ns1, s->rmin, s->nr1, nchains, (V*)sc.U);
+    }
+    const int nb = vec_blocks(s->N);
+    if (m3)
+        k_prolong<T, true><<<nb, BSE_VEC_THREADS, 0, st>>>((const V*)sc.R, (const V*)sc.U, (const V*)s->d_Dv,
+                                                          (const V*)s->d_Dc, (const T*)s->d_dE, psi, s->n, s->nd, s->nv,
+                                                          s->nc, s->nb1, nchains, s->N, c->Nc, W, sc.dot);
+    else
+        k_prolong<T, false><<<nb, BSE_VEC_THREADS, 0, st>>>((const V*)sc.R, nullptr, (const V*)s->d_Dv,
+                                                           (const V*)s->d_Dc, (const T*)s->d_dE, psi, s->n, s->nd, s->nv,
+                                                           s->nc, s->nb1, nchains, s->N, c->Nc, W, sc.dot);
+    return BSE_OK;
+}
+
+}  // namespace
+
+int bse_apply_scratch(bse_ctx* ctx, const bse_interp* s, int nvec, const void* x, void* y, const ApplyScratch& sc) {
+    return (s->vec_prec == BSE_PREC_F64) ? apply_scratch_typed<double>(ctx, s, nvec, x, y, sc)
+                                         : apply_scratch_typed<float>(ctx, s, nvec, x, y, sc);
+}

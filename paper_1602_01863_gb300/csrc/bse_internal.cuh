@@ -194,3 +194,18 @@ int bse_cf_device(bse_ctx* ctx, int nchains, int nsteps, const int* steps_done, 
 int bse_tc_prepare(bse_ctx* ctx, bse_interp* s);
 int bse_tc_apply(bse_ctx* ctx, bse_interp* s, int nchains);
 void bse_tc_release(bse_interp* s);
+
+// Per-call scratch of one H application, supplied by the caller instead of the
+// handle (used by the no-allocation entry point, bse_noalloc.cu).
+struct ApplyScratch {
+    void* Q;                 // V [nvec][Nc]       (complex128 / complex64 paths)
+    void* R;                 // V [nvec][Nc]
+    void* X;                 // V [nvec][nk][8][t] (M3 only)
+    void* U;                 // V [nvec][nk][8][t] (M3 only)
+    double2* dot;            // [nvec][BSE_MAX_VEC_BLOCKS]
+    __nv_bfloat16* bop;      // [16][ldk]          (BF16 path only)
+    float* part;             // tile partials      (BF16 path only)
+};
+size_t bse_tc_part_bytes(const bse_interp* s);
+int bse_tc_apply_scratch(bse_ctx* ctx, const bse_interp* s, int nchains, __nv_bfloat16* bop, float* part, void* R);
+int bse_apply_scratch(bse_ctx* ctx, const bse_interp* s, int nvec, const void* x, void* y, const ApplyScratch& sc);

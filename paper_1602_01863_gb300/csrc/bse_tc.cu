@@ -416,3 +416,26 @@ int bse_tc_apply(bse_ctx* ctx, bse_interp* s, int nchains) {
                                                              p.seg_max, c->Nc, nchains, (float2*)s->d_R);
     return BSE_OK;
 }
+
+// Bytes of the tile partials one tensor-core K_c apply writes.
+size_t bse_tc_part_bytes(const bse_interp* s) {
+    const TcState* st = reinterpret_cast<const TcState*>(s->tc_state);
+    return sizeof(float) * (size_t)st->plan.ctas * st->plan.seg_max * BM * 32;
+}
+
+// Tensor-core K_c apply with a caller-supplied operand buffer `bop` [16][ldk]
+// (zeroed by the caller where unused), tile partials `part` and output R: a
+// tensor map for `bop` is encoded on the stack; nothing is allocated.
+int bse_tc_apply_scratch(bse_ctx* ctx, const bse_interp* s, int nchains, __nv_bfloat16* bop, float* part, void* R) {
+    const bse_coarse* c = s->co;
+    const TcState* st = reinterpret_cast<const TcState*>(s->tc_state);
+    const TcPlan& p = st->plan;
+    CUtensorMap map_b;
+    int rc = make_map(ctx, &map_b, bop, c->ldk, BN, BN);
+    if (rc != BSE_OK) return rc;
+    k_tc_apply<<<p.ctas, TC_THREADS, STAGES * STAGE_BYTES + 1024, ctx->stream>>>(
+        st->map_kr, st->map_ki, map_b, p.kblocks_per_row, p.total, p.seg_max, part, ctx->d_status);
+    k_tc_reduce<<<(c->Nc + 127) / 128, 128, 0, ctx->stream>>>(part, st->d_tile_cta, st->d_q0, p.kblocks_per_row,
+                                                             p.seg_max, c->Nc, nchains, (float2*)R);
+    return BSE_OK;
+}
