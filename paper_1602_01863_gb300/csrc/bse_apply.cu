@@ -200,6 +200,132 @@ __global__ void __launch_bounds__(256) k_near_field(
     }
 }
 
+// Method 3 correction, one CTA per (coarse cell C, chain): all N_div targets
+// of C share the corners k~_l = C + l, the slots k~_s = C + o_s and hence the
+// head blocks.  For each slot s:
+//   (a) stage the slot's source rows x(k', k~_s) in shared memory: the pair
+//       (js', l') of the active list names source cell C + o_s - l';
+//   (b) y1(k, s) = sum h_head(q_dense) x, z(k, s) = sum x over the near sources
+//       of every target k (per-(js, s) lists built at set-up);
+//   (c) u(k, l) += Hv [y1 - h_head(q_coarse) z] Hc^T in factored form: each
+//       thread owns one row n1 of one active (target, corner) pair, forms
+//       T_row = G_row Hc^T, and gathers the other rows of T from its lane
+//       group (NVP lanes, NVP >= nv a power of two) by shuffles.
+template <typename T, int NVP>
+__global__ void __launch_bounds__(512) k_near_cell(
+    const typename Cx<T>::V* __restrict__ X, const int* __restrict__ clist, const int* __restrict__ cstart,
+    const int* __restrict__ pairs, int npairs, const T* __restrict__ hd, int n_near,
+    const typename Cx<T>::V* __restrict__ Hv, const typename Cx<T>::V* __restrict__ Hc, const T* __restrict__ hc,
+    int n, int nd, int nv, int nc, int smin, int ns1, int rmin, int nr1, typename Cx<T>::V* __restrict__ U) {
+    using V = typename Cx<T>::V;
+    constexpr int MAXNC = BSE_MAX_BANDS;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int t = nv * nc, Ndiv = nd * nd * nd, nslot = ns1 * ns1 * ns1, nrel = nr1 * nr1 * nr1;
+    const int nk = n * n * n * Ndiv;
+    const int cell = blockIdx.x, ch = blockIdx.y;
+    V* Xb = reinterpret_cast<V*>(smem_raw);          // [npairs][t]  staged source rows
+    V* Ua = Xb + (size_t)npairs * t;                  // [npairs][t]  accumulated u
+    V* Y1 = Ua + (size_t)npairs * t;                  // [Ndiv][t]
+    V* Zs = Y1 + (size_t)Ndiv * t;                    // [Ndiv][t]
+    V* Hvs = Zs + (size_t)Ndiv * t;                   // [8][nv*nv]
+    V* Hcs = Hvs + 8 * nv * nv;                       // [8][nc*nc]
+    T* hcs = reinterpret_cast<T*>(Hcs + 8 * nc * nc); // [8]
+    T* hds = hcs + 8;                                 // [n_near]
+    const Int3 ci = unflat3(cell, n);
+    const V* Xc = X + (size_t)ch * nk * 8 * t;
+    const int tid = threadIdx.x, bd = blockDim.x;
+    for (int i = tid; i < n_near; i += bd) hds[i] = hd[i];
+    for (int i = tid; i < npairs * t; i += bd) Ua[i] = czero<V>();
+    const int lane = tid & 31, gbase = lane & ~(NVP - 1);
+    for (int s = 0; s < nslot; ++s) {
+        const Int3 so = unflat3(s, ns1);
+        const int oa = so.a + smin, ob = so.b + smin, oc = so.c + smin;
+        // (a) source rows and the head blocks of the 8 corners
+        for (int idx = tid; idx < npairs * t; idx += bd) {
+            const int p = idx / t, e = idx - p * t;
+            const int pk = pairs[p], js = pk & 0xFFFF, l = pk >> 16;
+            const int sc = flat3(ci.a + oa - ((l >> 2) & 1), ci.b + ob - ((l >> 1) & 1), ci.c + oc - (l & 1), n);
+            Xb[idx] = Xc[(((size_t)sc * Ndiv + js) * 8 + l) * t + e];
+        }
+        for (int idx = tid; idx < 8 * (nv * nv + nc * nc + 1); idx += bd) {
+            const int l = idx % 8, q = idx / 8;
+            const int l1 = (l >> 2) & 1, l2 = (l >> 1) & 1, l3 = l & 1;
+            const int kt = flat3(ci.a + l1, ci.b + l2, ci.c + l3, n);
+            const int r = ((oa - l1 - rmin) * nr1 + (ob - l2 - rmin)) * nr1 + (oc - l3 - rmin);
+            if (q < nv * nv) Hvs[l * nv * nv + q] = Hv[((size_t)kt * nrel + r) * nv * nv + q];
+            else if (q < nv * nv + nc * nc) Hcs[l * nc * nc + (q - nv * nv)] = Hc[((size_t)kt * nrel + r) * nc * nc + (q - nv * nv)];
+            else hcs[l] = hc[r];
+        }
+        __syncthreads();
+        // (b) y1, z for every target of the cell
+        const int* cs = cstart + s;
+        for (int idx = tid; idx < Ndiv * t; idx += bd) {
+            const int j = idx / t, e = idx - j * t;
+            V y = czero<V>(), z = czero<V>();
+            const int q1 = cs[(size_t)j * (nslot + 1) + 1];
+            for (int q = cs[(size_t)j * (nslot + 1)]; q < q1; ++q) {
+                const int en = clist[q];
+                const V xv = Xb[(en & 0xFFFF) * t + e];
+                y = cadd(y, cscale(xv, hds[en >> 16]));
+                z = cadd(z, xv);
+            }
+            Y1[idx] = y;
+            Zs[idx] = z;
+        }
+        __syncthreads();
+        // (c) factored head application
+        for (int base = 0; base < npairs * NVP; base += bd) {
+            const int item = base + tid;
+            const int p = item / NVP, n1 = item % NVP;
+            const bool valid = (p < npairs) && (n1 < nv);
+            int j = 0, l = 0;
+            if (valid) { const int pk = pairs[p]; j = pk & 0xFFFF; l = pk >> 16; }
+            V trow[MAXNC];
+#pragma unroll
+            for (int n2 = 0; n2 < MAXNC; ++n2) trow[n2] = czero<V>();
+            if (valid) {
+                const T hcl = hcs[l];
+                const V* y = Y1 + j * t + n1 * nc;
+                const V* z = Zs + j * t + n1 * nc;
+                const V* hcm = Hcs + l * nc * nc;
+                for (int n4 = 0; n4 < nc; ++n4) {
+                    const V g = csub(y[n4], cscale(z[n4], hcl));
+#pragma unroll
+                    for (int n2 = 0; n2 < MAXNC; ++n2)
+                        if (n2 < nc) trow[n2] = cadd(trow[n2], cmul(g, hcm[n2 * nc + n4]));
+                }
+            }
+            V acc[MAXNC];
+#pragma unroll
+            for (int n2 = 0; n2 < MAXNC; ++n2) acc[n2] = czero<V>();
+            for (int n3 = 0; n3 < nv; ++n3) {
+                const V hv = valid ? Hvs[l * nv * nv + n1 * nv + n3] : czero<V>();
+#pragma unroll
+                for (int n2 = 0; n2 < MAXNC; ++n2) {
+                    if (n2 < nc) {
+                        V tv;
+                        tv.x = __shfl_sync(0xffffffffu, trow[n2].x, gbase + n3);
+                        tv.y = __shfl_sync(0xffffffffu, trow[n2].y, gbase + n3);
+                        acc[n2] = cadd(acc[n2], cmul(hv, tv));
+                    }
+                }
+            }
+            if (valid) {
+                V* ua = Ua + (size_t)p * t + n1 * nc;
+#pragma unroll
+                for (int n2 = 0; n2 < MAXNC; ++n2)
+                    if (n2 < nc) ua[n2] = cadd(ua[n2], acc[n2]);
+            }
+        }
+        __syncthreads();
+    }
+    for (int idx = tid; idx < npairs * t; idx += bd) {
+        const int p = idx / t, e = idx - p * t;
+        const int pk = pairs[p], j = pk & 0xFFFF, l = pk >> 16;
+        U[(((size_t)ch * nk + (size_t)cell * Ndiv + j) * 8 + l) * t + e] = Ua[idx];
+    }
+}
+
 // ------------------------------------------------------- prolong + diagonal
 // w = dE psi + (1/N_div) sum_l f Dv^T (R(k~_l) + u(k, l)) conj(Dc); one thread
 // per dense element (kd, v, c) serving all chains; block partials of <psi, w>.
@@ -553,13 +679,8 @@ int apply_h_typed(bse_ctx* ctx, bse_interp* s, int nchains, const void* psi_v, v
     }
     if (m3) {
         Timer tm(ctx, prof, KC_NEAR);
-        const size_t smem = sizeof(V) * 2 * s->nslot * s->t;
-        if (smem > 48 * 1024) {
-            BSE_CUDA_TRY(ctx, cudaFuncSetAttribute(k_near_field<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        }
-        k_near_field<T><<<s->nk, 256, smem, st>>>(X, s->d_list, s->d_list_start, (const T*)s->d_hd, (const V*)s->d_Hv,
-                                                 (const V*)s->d_Hc, (const T*)s->d_hc, s->n, s->nd, s->nv, s->nc, s->nb1,
-                                                 s->smin, s->ns1, s->rmin, s->nr1, nchains, (V*)s->d_U);
+        int rc = bse_launch_near_field(ctx, s, nchains, X, s->d_U);
+        if (rc != BSE_OK) return rc;
     }
     {
         Timer tm(ctx, prof, KC_PROLONG);
@@ -816,13 +937,8 @@ int apply_scratch_typed(bse_ctx* ctx, const bse_interp* s, int nchains, const vo
         k_kc_apply_simt<T><<<(c->Nc + 7) / 8, 256, 0, st>>>((const V*)c->d_kc, (const V*)sc.Q, c->Nc, nchains, (V*)sc.R);
     }
     if (m3) {
-        const size_t smem = sizeof(V) * 2 * s->nslot * s->t;
-        if (smem > 48 * 1024) {
-            BSE_CUDA_TRY(ctx, cudaFuncSetAttribute(k_near_field<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        }
-        k_near_field<T><<<s->nk, 256, smem, st>>>(X, s->d_list, s->d_list_start, (const T*)s->d_hd, (const V*)s->d_Hv,
-                                                 (const V*)s->d_Hc, (const T*)s->d_hc, s->n, s->nd, s->nv, s->nc, s->nb1,
-                                                 s->smin, s->ns1, s->rmin, s->nr1, nchains, (V*)sc.U);
+        int rc = bse_launch_near_field(ctx, s, nchains, X, sc.U);
+        if (rc != BSE_OK) return rc;
     }
     const int nb = vec_blocks(s->N);
     if (m3)
@@ -841,4 +957,46 @@ int apply_scratch_typed(bse_ctx* ctx, const bse_interp* s, int nchains, const vo
 int bse_apply_scratch(bse_ctx* ctx, const bse_interp* s, int nvec, const void* x, void* y, const ApplyScratch& sc) {
     return (s->vec_prec == BSE_PREC_F64) ? apply_scratch_typed<double>(ctx, s, nvec, x, y, sc)
                                          : apply_scratch_typed<float>(ctx, s, nvec, x, y, sc);
+}
+
+namespace {
+
+template <typename T, int NVP>
+int launch_near_cell(bse_ctx* ctx, const bse_interp* s, int nchains, const void* X, void* U) {
+    using V = typename Cx<T>::V;
+    const int smem = (int)s->cell_smem;
+    if (smem > 48 * 1024)
+        BSE_CUDA_TRY(ctx, cudaFuncSetAttribute(k_near_cell<T, NVP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    dim3 grid(s->co->nkc, nchains);
+    k_near_cell<T, NVP><<<grid, 512, smem, ctx->stream>>>(
+        (const V*)X, s->d_clist, s->d_cstart, s->d_pairs, s->npairs, (const T*)s->d_hd, s->n_near, (const V*)s->d_Hv,
+        (const V*)s->d_Hc, (const T*)s->d_hc, s->n, s->nd, s->nv, s->nc, s->smin, s->ns1, s->rmin, s->nr1, (V*)U);
+    return BSE_OK;
+}
+
+template <typename T>
+int launch_near_typed(bse_ctx* ctx, const bse_interp* s, int nchains, const void* X, void* U) {
+    using V = typename Cx<T>::V;
+    if (s->cell_smem) {
+        if (s->nv <= 1) return launch_near_cell<T, 1>(ctx, s, nchains, X, U);
+        if (s->nv <= 2) return launch_near_cell<T, 2>(ctx, s, nchains, X, U);
+        if (s->nv <= 4) return launch_near_cell<T, 4>(ctx, s, nchains, X, U);
+        return launch_near_cell<T, 8>(ctx, s, nchains, X, U);
+    }
+    const size_t smem = sizeof(V) * 2 * s->nslot * s->t;
+    if (smem > 48 * 1024)
+        BSE_CUDA_TRY(ctx, cudaFuncSetAttribute(k_near_field<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_near_field<T><<<s->nk, 256, smem, ctx->stream>>>((const V*)X, s->d_list, s->d_list_start, (const T*)s->d_hd,
+                                                      (const V*)s->d_Hv, (const V*)s->d_Hc, (const T*)s->d_hc, s->n,
+                                                      s->nd, s->nv, s->nc, s->nb1, s->smin, s->ns1, s->rmin, s->nr1,
+                                                      nchains, (V*)U);
+    return BSE_OK;
+}
+
+}  // namespace
+
+// M3 near field for nchains chains: X pieces in, u pieces out (both [chain][nk][8][t]).
+int bse_launch_near_field(bse_ctx* ctx, const bse_interp* s, int nchains, const void* X, void* U) {
+    return (s->vec_prec == BSE_PREC_F64) ? launch_near_typed<double>(ctx, s, nchains, X, U)
+                                         : launch_near_typed<float>(ctx, s, nchains, X, U);
 }

@@ -133,6 +133,13 @@ struct bse_interp {
     int n_near = 0, smin = 0, ns1 = 0, nslot = 0, rmin = 0, nr1 = 0, nrel = 0;
     NearEntry* d_list = nullptr;
     int* d_list_start = nullptr;     // [Ndiv][nslot + 1]
+    // cell-batched near field: active (js, corner) pairs and per-(js, slot)
+    // contribution lists (source pair index | near-offset index << 16)
+    int npairs = 0;
+    int* d_pairs = nullptr;          // [npairs]  js | corner << 16
+    int* d_clist = nullptr;
+    int* d_cstart = nullptr;         // [Ndiv][nslot + 1]
+    size_t cell_smem = 0;            // dynamic shared memory of the cell kernel (0: not usable)
     void* d_hd = nullptr;            // T [n_near]   h_head at dense near offsets
     void* d_Hv = nullptr;            // V [nkc][nrel][nv*nv]
     void* d_Hc = nullptr;            // V [nkc][nrel][nc*nc]
@@ -206,6 +213,7 @@ struct ApplyScratch {
     __nv_bfloat16* bop;      // [16][ldk]          (BF16 path only)
     float* part;             // tile partials      (BF16 path only)
 };
+int bse_launch_near_field(bse_ctx* ctx, const bse_interp* s, int nchains, const void* X, void* U);
 size_t bse_tc_part_bytes(const bse_interp* s);
 int bse_tc_apply_scratch(bse_ctx* ctx, const bse_interp* s, int nchains, __nv_bfloat16* bop, float* part, void* R);
 int bse_apply_scratch(bse_ctx* ctx, const bse_interp* s, int nvec, const void* x, void* y, const ApplyScratch& sc);

@@ -502,6 +502,43 @@ int setup_interp_typed(bse_ctx* ctx, bse_interp* s) {
         TRY(bse_alloc(ctx, (void**)&s->d_list_start, sizeof(int) * start.size(), "near list starts"));
         BSE_CUDA_TRY(ctx, cudaMemcpy(s->d_list, flat.data(), sizeof(NearEntry) * flat.size(), cudaMemcpyHostToDevice));
         BSE_CUDA_TRY(ctx, cudaMemcpy(s->d_list_start, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice));
+        // Cell-batched form: the same contributions, with the source named by its
+        // (js', corner) pair index, so one coarse cell's targets share a slot's
+        // source rows staged in shared memory.
+        {
+            std::vector<int> pairs, pidx((size_t)Ndiv * 8, -1);
+            for (int js = 0; js < Ndiv; ++js)
+                for (int l = 0; l < 8; ++l)
+                    if (interp_weight(js, l, nd, s->nb1) != 0.0) {
+                        pidx[(size_t)js * 8 + l] = (int)pairs.size();
+                        pairs.push_back(js | (l << 16));
+                    }
+            s->npairs = (int)pairs.size();
+            std::vector<int> clist, cstart((size_t)Ndiv * (s->nslot + 1));
+            for (int js = 0; js < Ndiv; ++js) {
+                for (int sl = 0; sl < s->nslot; ++sl) {
+                    cstart[(size_t)js * (s->nslot + 1) + sl] = (int)clist.size();
+                    for (const NearEntry& en : per_slot[(size_t)js * s->nslot + sl])
+                        clist.push_back(pidx[(size_t)en.js_src * 8 + en.l_src] | (en.near_idx << 16));
+                }
+                cstart[(size_t)js * (s->nslot + 1) + s->nslot] = (int)clist.size();
+            }
+            const size_t vs = sizeof(V), ts = sizeof(T);
+            const size_t smem = vs * (2 * (size_t)s->npairs * t + 2 * (size_t)Ndiv * t + 8 * (nv * nv + nc * nc)) +
+                                ts * (8 + (size_t)s->n_near);
+            int maxsm = 0;
+            cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+            const bool fits = s->n_near < 65536 && s->npairs < 65536 && smem + 1024 <= (size_t)maxsm;
+            s->cell_smem = fits ? smem : 0;
+            if (fits) {
+                TRY(bse_alloc(ctx, (void**)&s->d_pairs, sizeof(int) * pairs.size(), "near pairs"));
+                TRY(bse_alloc(ctx, (void**)&s->d_clist, sizeof(int) * clist.size(), "cell near list"));
+                TRY(bse_alloc(ctx, (void**)&s->d_cstart, sizeof(int) * cstart.size(), "cell near list starts"));
+                BSE_CUDA_TRY(ctx, cudaMemcpy(s->d_pairs, pairs.data(), sizeof(int) * pairs.size(), cudaMemcpyHostToDevice));
+                BSE_CUDA_TRY(ctx, cudaMemcpy(s->d_clist, clist.data(), sizeof(int) * clist.size(), cudaMemcpyHostToDevice));
+                BSE_CUDA_TRY(ctx, cudaMemcpy(s->d_cstart, cstart.data(), sizeof(int) * cstart.size(), cudaMemcpyHostToDevice));
+            }
+        }
         int* d_offs = nullptr;
         double* d_hh = nullptr;
         TRY(bse_alloc(ctx, (void**)&d_offs, sizeof(int) * offs.size(), "near offsets"));
