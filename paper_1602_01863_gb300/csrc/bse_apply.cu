@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "bse_internal.cuh"
 
@@ -32,47 +33,70 @@ __global__ void __launch_bounds__(256) k_restrict(
     int N, int Nc, typename Cx<T>::V* __restrict__ Q, __nv_bfloat16* __restrict__ Bop, int ldk,
     typename Cx<T>::V* __restrict__ X, const int* __restrict__ stop) {
     using V = typename Cx<T>::V;
-    __shared__ V red[kRestrictWarps][BSE_MAX_CHAINS][BSE_MAX_T];
+    // per-warp staging of one (source point, corner) pair: psi rows of all
+    // chains, Dv and Dc; reused at the end for the cross-warp reduction
+    constexpr int WS = BSE_MAX_CHAINS * BSE_MAX_T + 2 * BSE_MAX_T;
+    __shared__ V sm[kRestrictWarps * WS];
     const int t = nv * nc;
     const int Ndiv = nd * nd * nd;
     const int ic = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const Int3 i = unflat3(ic, n);
+    V* wps = sm + warp * WS;
+    V* wdv = wps + BSE_MAX_CHAINS * BSE_MAX_T;
+    V* wdc = wdv + BSE_MAX_T;
     V acc[BSE_MAX_CHAINS][2];
 #pragma unroll
     for (int ch = 0; ch < BSE_MAX_CHAINS; ++ch) { acc[ch][0] = czero<V>(); acc[ch][1] = czero<V>(); }
+    int n3q[2], n4q[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) { const int e = lane + 32 * q; n3q[q] = e / nc; n4q[q] = e % nc; }
     for (int p = warp; p < 8 * Ndiv; p += kRestrictWarps) {
         const int l = p / Ndiv, js = p % Ndiv;
         const T f = (T)interp_weight(js, l, nd, nb1);
-        if (f == (T)0) continue;
+        if (f == (T)0) continue;                                   // warp-uniform
         const int src = flat3(i.a - ((l >> 2) & 1), i.b - ((l >> 1) & 1), i.c - (l & 1), n);
         const size_t kd = (size_t)src * Ndiv + js;
         const V* dv = Dv + (kd * 8 + l) * nv * nv;
         const V* dc = Dc + (kd * 8 + l) * nc * nc;
+        for (int ch = 0; ch < nchains; ++ch)
+            for (int e = lane; e < t; e += 32) wps[ch * BSE_MAX_T + e] = psi[(size_t)ch * N + kd * t + e];
+        for (int e = lane; e < nv * nv; e += 32) wdv[e] = dv[e];
+        for (int e = lane; e < nc * nc; e += 32) wdc[e] = dc[e];
+        __syncwarp();
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
             const int e = lane + 32 * q;
             if (e >= t) break;
-            const int n3 = e / nc, n4 = e % nc;
-            for (int ch = 0; ch < nchains; ++ch) {
-                const V* ps = psi + (size_t)ch * N + kd * t;
+            const int n3 = n3q[q], n4 = n4q[q];
+#pragma unroll
+            for (int ch = 0; ch < BSE_MAX_CHAINS; ++ch) {
+                if (ch >= nchains) break;
+                const V* ps = wps + ch * BSE_MAX_T;
                 V x = czero<V>();
                 for (int vp = 0; vp < nv; ++vp) {
                     V inner = czero<V>();
-                    for (int cp = 0; cp < nc; ++cp) inner = cadd(inner, cmul(ps[vp * nc + cp], dc[n4 * nc + cp]));
-                    x = cadd(x, cmulc(dv[n3 * nv + vp], inner));
+                    for (int cp = 0; cp < nc; ++cp) inner = cadd(inner, cmul(ps[vp * nc + cp], wdc[n4 * nc + cp]));
+                    x = cadd(x, cmulc(wdv[n3 * nv + vp], inner));
                 }
                 x = cscale(x, f);
                 if (X) X[(((size_t)ch * (N / t) + kd) * 8 + l) * t + e] = x;
                 acc[ch][q] = cadd(acc[ch][q], x);
             }
         }
+        __syncwarp();
     }
-    for (int ch = 0; ch < nchains; ++ch)
+    __syncthreads();
+    V (*red)[BSE_MAX_CHAINS][BSE_MAX_T] = reinterpret_cast<V (*)[BSE_MAX_CHAINS][BSE_MAX_T]>(sm);
+#pragma unroll
+    for (int ch = 0; ch < BSE_MAX_CHAINS; ++ch) {
+        if (ch >= nchains) break;
+#pragma unroll
         for (int q = 0; q < 2; ++q) {
             const int e = lane + 32 * q;
             if (e < t) red[warp][ch][e] = acc[ch][q];
         }
+    }
     __syncthreads();
     for (int idx = threadIdx.x; idx < nchains * t; idx += blockDim.x) {
         const int ch = idx / t, e = idx % t;
@@ -93,6 +117,222 @@ __global__ void __launch_bounds__(256) k_restrict(
         }
     }
     (void)stop;
+}
+
+// Register-blocked restrict (FP32, compile-time band counts): one thread per
+// (corner l, sub-point js) candidate of the target coarse point; x = f conj(Dv)
+// psi Dc^T is formed row by row (Dc in registers), summed per thread, then
+// over the block in a fixed order (two stages through shared memory).
+template <int NV, int NC, bool OUT_BF16>
+__global__ void __launch_bounds__(256) k_restrict_rb(
+    const float2* __restrict__ psi, const float2* __restrict__ Dv, const float2* __restrict__ Dc, int n, int nd,
+    int nb1, int nchains, int N, int Nc, float2* __restrict__ Q, __nv_bfloat16* __restrict__ Bop, int ldk,
+    float2* __restrict__ X) {
+    constexpr int t = NV * NC, tp = t + 1;
+    constexpr int NG = 256 / t;                                // row groups of the block reduction
+    __shared__ float2 red[256 * tp];
+    __shared__ float2 part[NG * t];
+    const int Ndiv = nd * nd * nd;
+    const int ic = blockIdx.x, tid = threadIdx.x;
+    const Int3 i = unflat3(ic, n);
+    for (int ch = 0; ch < nchains; ++ch) {
+        float2 acc[NV][NC];
+#pragma unroll
+        for (int a = 0; a < NV; ++a)
+#pragma unroll
+            for (int b = 0; b < NC; ++b) acc[a][b] = make_float2(0.f, 0.f);
+        for (int cand = tid; cand < 8 * Ndiv; cand += 256) {
+            const int l = cand / Ndiv, js = cand - l * Ndiv;
+            const float f = (float)interp_weight(js, l, nd, nb1);
+            if (f == 0.f) continue;
+            const int src = flat3(i.a - ((l >> 2) & 1), i.b - ((l >> 1) & 1), i.c - (l & 1), n);
+            const size_t kd = (size_t)src * Ndiv + js;
+            const float2* dv = Dv + (kd * 8 + l) * NV * NV;
+            const float2* dcp = Dc + (kd * 8 + l) * NC * NC;
+            const float2* ps = psi + (size_t)ch * N + kd * t;
+            float2 dc[NC][NC];
+#pragma unroll
+            for (int a = 0; a < NC; ++a)
+#pragma unroll
+                for (int b = 0; b < NC; ++b) dc[a][b] = dcp[a * NC + b];
+            float2 x[NV][NC];
+#pragma unroll
+            for (int a = 0; a < NV; ++a)
+#pragma unroll
+                for (int b = 0; b < NC; ++b) x[a][b] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int vp = 0; vp < NV; ++vp) {
+                float2 pr[NC];
+#pragma unroll
+                for (int cp = 0; cp < NC; ++cp) pr[cp] = ps[vp * NC + cp];
+                float2 t1[NC];                                  // t1[n4] = sum_c' psi[vp][c'] Dc[n4][c']
+#pragma unroll
+                for (int n4 = 0; n4 < NC; ++n4) {
+                    float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int cp = 0; cp < NC; ++cp) {
+                        s.x = fmaf(pr[cp].x, dc[n4][cp].x, fmaf(-pr[cp].y, dc[n4][cp].y, s.x));
+                        s.y = fmaf(pr[cp].x, dc[n4][cp].y, fmaf(pr[cp].y, dc[n4][cp].x, s.y));
+                    }
+                    t1[n4] = s;
+                }
+#pragma unroll
+                for (int n3 = 0; n3 < NV; ++n3) {
+                    const float2 d = dv[n3 * NV + vp];             // x += conj(Dv[n3][vp]) t1
+#pragma unroll
+                    for (int n4 = 0; n4 < NC; ++n4) {
+                        x[n3][n4].x = fmaf(d.x, t1[n4].x, fmaf(d.y, t1[n4].y, x[n3][n4].x));
+                        x[n3][n4].y = fmaf(d.x, t1[n4].y, fmaf(-d.y, t1[n4].x, x[n3][n4].y));
+                    }
+                }
+            }
+            float2* xo = X ? X + (((size_t)ch * (N / t) + kd) * 8 + l) * t : nullptr;
+#pragma unroll
+            for (int a = 0; a < NV; ++a)
+#pragma unroll
+                for (int b = 0; b < NC; ++b) {
+                    const float2 v = make_float2(x[a][b].x * f, x[a][b].y * f);
+                    if (xo) xo[a * NC + b] = v;
+                    acc[a][b].x += v.x;
+                    acc[a][b].y += v.y;
+                }
+        }
+#pragma unroll
+        for (int a = 0; a < NV; ++a)
+#pragma unroll
+            for (int b = 0; b < NC; ++b) red[tid * tp + a * NC + b] = acc[a][b];
+        __syncthreads();
+        if (tid < NG * t) {
+            const int e = tid % t, g = tid / t;
+            float2 s = make_float2(0.f, 0.f);
+            for (int r = g; r < 256; r += NG) {
+                const float2 v = red[r * tp + e];
+                s.x += v.x;
+                s.y += v.y;
+            }
+            part[g * t + e] = s;
+        }
+        __syncthreads();
+        if (tid < t) {
+            float2 s = part[tid];
+            for (int g = 1; g < NG; ++g) {
+                const float2 v = part[g * t + tid];
+                s.x += v.x;
+                s.y += v.y;
+            }
+            const int row = ic * t + tid;
+            if (!OUT_BF16) {
+                Q[(size_t)ch * Nc + row] = s;
+            } else {
+                const __nv_bfloat16 rh = __float2bfloat16_rn(s.x), ih = __float2bfloat16_rn(s.y);
+                Bop[(size_t)ch * ldk + row] = rh;
+                Bop[(size_t)(nchains + ch) * ldk + row] = ih;
+                Bop[(size_t)(2 * nchains + ch) * ldk + row] = __float2bfloat16_rn(s.x - __bfloat162float(rh));
+                Bop[(size_t)(3 * nchains + ch) * ldk + row] = __float2bfloat16_rn(s.y - __bfloat162float(ih));
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Register-blocked prolong + diagonal (FP32): one thread per (chain, dense
+// point); per corner T = M conj(Dc) is formed row by row (Dc in registers)
+// and Dv^T T accumulated; block partials of <psi, w> as in k_prolong.
+template <int NV, int NC, bool NEAR>
+__global__ void __launch_bounds__(BSE_VEC_THREADS) k_prolong_rb(
+    const float2* __restrict__ R, const float2* __restrict__ Unf, const float2* __restrict__ Dv,
+    const float2* __restrict__ Dc, const float* __restrict__ dE, const float2* __restrict__ psi, int n, int nd,
+    int nb1, int nchains, int N, int Nc, float2* __restrict__ W, double2* __restrict__ part) {
+    constexpr int t = NV * NC;
+    __shared__ double2 red[BSE_MAX_CHAINS][BSE_VEC_THREADS];
+    const int Ndiv = nd * nd * nd;
+    const int nk = N / t;
+    const float inv_ndiv = 1.f / (float)Ndiv;
+    double2 dot[BSE_MAX_CHAINS];
+#pragma unroll
+    for (int c = 0; c < BSE_MAX_CHAINS; ++c) dot[c] = make_double2(0.0, 0.0);
+    const long long total = (long long)nchains * nk;
+    for (long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x; gid < total;
+         gid += (long long)gridDim.x * blockDim.x) {
+        const int ch = (int)(gid / nk), kd = (int)(gid - (long long)ch * nk);
+        const int cell = kd / Ndiv, js = kd - cell * Ndiv;
+        const Int3 ci = unflat3(cell, n);
+        float2 s[NV][NC];
+#pragma unroll
+        for (int a = 0; a < NV; ++a)
+#pragma unroll
+            for (int b = 0; b < NC; ++b) s[a][b] = make_float2(0.f, 0.f);
+        for (int l = 0; l < 8; ++l) {
+            const float f = (float)interp_weight(js, l, nd, nb1);
+            if (f == 0.f) continue;
+            const int cc = flat3(ci.a + ((l >> 2) & 1), ci.b + ((l >> 1) & 1), ci.c + (l & 1), n);
+            const float2* dv = Dv + ((size_t)kd * 8 + l) * NV * NV;
+            const float2* dcp = Dc + ((size_t)kd * 8 + l) * NC * NC;
+            const float2* rr = R + (size_t)ch * Nc + (size_t)cc * t;
+            const float2* uu = NEAR ? Unf + (((size_t)ch * nk + kd) * 8 + l) * t : nullptr;
+            float2 dc[NC][NC];
+#pragma unroll
+            for (int a = 0; a < NC; ++a)
+#pragma unroll
+                for (int b = 0; b < NC; ++b) dc[a][b] = dcp[a * NC + b];
+#pragma unroll
+            for (int n1 = 0; n1 < NV; ++n1) {
+                float2 m[NC];
+#pragma unroll
+                for (int n2 = 0; n2 < NC; ++n2) {
+                    m[n2] = rr[n1 * NC + n2];
+                    if (NEAR) { const float2 u = uu[n1 * NC + n2]; m[n2].x += u.x; m[n2].y += u.y; }
+                }
+                float2 tr[NC];                                  // tr[c] = sum_n2 m[n2] conj(Dc[n2][c])
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int n2 = 0; n2 < NC; ++n2) {
+                        a.x = fmaf(m[n2].x, dc[n2][c].x, fmaf(m[n2].y, dc[n2][c].y, a.x));
+                        a.y = fmaf(m[n2].y, dc[n2][c].x, fmaf(-m[n2].x, dc[n2][c].y, a.y));
+                    }
+                    tr[c] = make_float2(a.x * f, a.y * f);
+                }
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    const float2 d = dv[n1 * NV + v];
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) {
+                        s[v][c].x = fmaf(d.x, tr[c].x, fmaf(-d.y, tr[c].y, s[v][c].x));
+                        s[v][c].y = fmaf(d.x, tr[c].y, fmaf(d.y, tr[c].x, s[v][c].y));
+                    }
+                }
+            }
+        }
+        const size_t base = (size_t)kd * t;
+        double2 dd = make_double2(0.0, 0.0);
+#pragma unroll
+        for (int a = 0; a < NV; ++a)
+#pragma unroll
+            for (int b = 0; b < NC; ++b) {
+                const int e = a * NC + b;
+                const float2 p = psi[(size_t)ch * N + base + e];
+                const float de = dE[base + e];
+                const float2 w = make_float2(fmaf(p.x, de, s[a][b].x * inv_ndiv), fmaf(p.y, de, s[a][b].y * inv_ndiv));
+                W[(size_t)ch * N + base + e] = w;
+                dd.x += (double)p.x * w.x + (double)p.y * w.y;
+                dd.y += (double)p.x * w.y - (double)p.y * w.x;
+            }
+#pragma unroll
+        for (int c = 0; c < BSE_MAX_CHAINS; ++c)
+            if (c == ch) { dot[c].x += dd.x; dot[c].y += dd.y; }
+    }
+#pragma unroll
+    for (int c = 0; c < BSE_MAX_CHAINS; ++c) red[c][threadIdx.x] = dot[c];
+    __syncthreads();
+    for (int st = BSE_VEC_THREADS / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st)
+#pragma unroll
+            for (int c = 0; c < BSE_MAX_CHAINS; ++c) red[c][threadIdx.x] = cadd(red[c][threadIdx.x], red[c][threadIdx.x + st]);
+        __syncthreads();
+    }
+    if (threadIdx.x < nchains) part[(size_t)threadIdx.x * BSE_MAX_VEC_BLOCKS + blockIdx.x] = red[threadIdx.x][0];
 }
 
 // ------------------------------------------------- K_c apply on CUDA cores
@@ -220,35 +460,49 @@ __global__ void __launch_bounds__(512) k_near_cell(
     using V = typename Cx<T>::V;
     constexpr int MAXNC = BSE_MAX_BANDS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int t = nv * nc, Ndiv = nd * nd * nd, nslot = ns1 * ns1 * ns1, nrel = nr1 * nr1 * nr1;
+    const int t = nv * nc, tp = t + 1, Ndiv = nd * nd * nd, nslot = ns1 * ns1 * ns1, nrel = nr1 * nr1 * nr1;
     const int nk = n * n * n * Ndiv;
     const int cell = blockIdx.x, ch = blockIdx.y;
-    V* Xb = reinterpret_cast<V*>(smem_raw);          // [npairs][t]  staged source rows
-    V* Ua = Xb + (size_t)npairs * t;                  // [npairs][t]  accumulated u
-    V* Y1 = Ua + (size_t)npairs * t;                  // [Ndiv][t]
-    V* Zs = Y1 + (size_t)Ndiv * t;                    // [Ndiv][t]
-    V* Hvs = Zs + (size_t)Ndiv * t;                   // [8][nv*nv]
+    // rows are padded to t + 1 elements so neighbouring rows start in different banks
+    V* Xb = reinterpret_cast<V*>(smem_raw);          // [npairs][tp]  staged source rows
+    V* Ua = Xb + (size_t)npairs * tp;                 // [npairs][tp]  accumulated u
+    V* Y1 = Ua + (size_t)npairs * tp;                 // [Ndiv][tp]
+    V* Zs = Y1 + (size_t)Ndiv * tp;                   // [Ndiv][tp]
+    V* Hvs = Zs + (size_t)Ndiv * tp;                  // [8][nv*nv]
     V* Hcs = Hvs + 8 * nv * nv;                       // [8][nc*nc]
     T* hcs = reinterpret_cast<T*>(Hcs + 8 * nc * nc); // [8]
     T* hds = hcs + 8;                                 // [n_near]
+    int* pcache = reinterpret_cast<int*>(hds + n_near);   // [npairs]   js | corner << 16
+    int* scell = pcache + npairs;                     // [nslot][8] source cell of (slot, corner)
     const Int3 ci = unflat3(cell, n);
     const V* Xc = X + (size_t)ch * nk * 8 * t;
     const int tid = threadIdx.x, bd = blockDim.x;
     for (int i = tid; i < n_near; i += bd) hds[i] = hd[i];
-    for (int i = tid; i < npairs * t; i += bd) Ua[i] = czero<V>();
+    for (int i = tid; i < npairs; i += bd) pcache[i] = pairs[i];
+    for (int i = tid; i < npairs * tp; i += bd) Ua[i] = czero<V>();
+    for (int i = tid; i < nslot * 8; i += bd) {
+        const int s = i >> 3, l = i & 7;
+        const Int3 so = unflat3(s, ns1);
+        scell[i] = flat3(ci.a + so.a + smin - ((l >> 2) & 1), ci.b + so.b + smin - ((l >> 1) & 1),
+                         ci.c + so.c + smin - (l & 1), n);
+    }
     const int lane = tid & 31, gbase = lane & ~(NVP - 1);
+    const int rows_per_pass = bd / t;                 // staging: thread -> (row, element) without division
+    const int e_st = tid % t, r_st = tid / t;
+    __syncthreads();
     for (int s = 0; s < nslot; ++s) {
         const Int3 so = unflat3(s, ns1);
         const int oa = so.a + smin, ob = so.b + smin, oc = so.c + smin;
         // (a) source rows and the head blocks of the 8 corners
-        for (int idx = tid; idx < npairs * t; idx += bd) {
-            const int p = idx / t, e = idx - p * t;
-            const int pk = pairs[p], js = pk & 0xFFFF, l = pk >> 16;
-            const int sc = flat3(ci.a + oa - ((l >> 2) & 1), ci.b + ob - ((l >> 1) & 1), ci.c + oc - (l & 1), n);
-            Xb[idx] = Xc[(((size_t)sc * Ndiv + js) * 8 + l) * t + e];
+        if (r_st < rows_per_pass) {
+            for (int p = r_st; p < npairs; p += rows_per_pass) {
+                const int pk = pcache[p], js = pk & 0xFFFF, l = pk >> 16;
+                const int sc = scell[s * 8 + l];
+                Xb[p * tp + e_st] = Xc[(((size_t)sc * Ndiv + js) * 8 + l) * t + e_st];
+            }
         }
         for (int idx = tid; idx < 8 * (nv * nv + nc * nc + 1); idx += bd) {
-            const int l = idx % 8, q = idx / 8;
+            const int l = idx & 7, q = idx >> 3;
             const int l1 = (l >> 2) & 1, l2 = (l >> 1) & 1, l3 = l & 1;
             const int kt = flat3(ci.a + l1, ci.b + l2, ci.c + l3, n);
             const int r = ((oa - l1 - rmin) * nr1 + (ob - l2 - rmin)) * nr1 + (oc - l3 - rmin);
@@ -259,18 +513,19 @@ __global__ void __launch_bounds__(512) k_near_cell(
         __syncthreads();
         // (b) y1, z for every target of the cell
         const int* cs = cstart + s;
-        for (int idx = tid; idx < Ndiv * t; idx += bd) {
-            const int j = idx / t, e = idx - j * t;
-            V y = czero<V>(), z = czero<V>();
-            const int q1 = cs[(size_t)j * (nslot + 1) + 1];
-            for (int q = cs[(size_t)j * (nslot + 1)]; q < q1; ++q) {
-                const int en = clist[q];
-                const V xv = Xb[(en & 0xFFFF) * t + e];
-                y = cadd(y, cscale(xv, hds[en >> 16]));
-                z = cadd(z, xv);
+        if (r_st < rows_per_pass) {
+            for (int j = r_st; j < Ndiv; j += rows_per_pass) {
+                V y = czero<V>(), z = czero<V>();
+                const int q1 = cs[(size_t)j * (nslot + 1) + 1];
+                for (int q = cs[(size_t)j * (nslot + 1)]; q < q1; ++q) {
+                    const int en = clist[q];
+                    const V xv = Xb[(en & 0xFFFF) * tp + e_st];
+                    y = cadd(y, cscale(xv, hds[en >> 16]));
+                    z = cadd(z, xv);
+                }
+                Y1[j * tp + e_st] = y;
+                Zs[j * tp + e_st] = z;
             }
-            Y1[idx] = y;
-            Zs[idx] = z;
         }
         __syncthreads();
         // (c) factored head application
@@ -279,14 +534,14 @@ __global__ void __launch_bounds__(512) k_near_cell(
             const int p = item / NVP, n1 = item % NVP;
             const bool valid = (p < npairs) && (n1 < nv);
             int j = 0, l = 0;
-            if (valid) { const int pk = pairs[p]; j = pk & 0xFFFF; l = pk >> 16; }
+            if (valid) { const int pk = pcache[p]; j = pk & 0xFFFF; l = pk >> 16; }
             V trow[MAXNC];
 #pragma unroll
             for (int n2 = 0; n2 < MAXNC; ++n2) trow[n2] = czero<V>();
             if (valid) {
                 const T hcl = hcs[l];
-                const V* y = Y1 + j * t + n1 * nc;
-                const V* z = Zs + j * t + n1 * nc;
+                const V* y = Y1 + j * tp + n1 * nc;
+                const V* z = Zs + j * tp + n1 * nc;
                 const V* hcm = Hcs + l * nc * nc;
                 for (int n4 = 0; n4 < nc; ++n4) {
                     const V g = csub(y[n4], cscale(z[n4], hcl));
@@ -311,7 +566,7 @@ __global__ void __launch_bounds__(512) k_near_cell(
                 }
             }
             if (valid) {
-                V* ua = Ua + (size_t)p * t + n1 * nc;
+                V* ua = Ua + (size_t)p * tp + n1 * nc;
 #pragma unroll
                 for (int n2 = 0; n2 < MAXNC; ++n2)
                     if (n2 < nc) ua[n2] = cadd(ua[n2], acc[n2]);
@@ -319,10 +574,144 @@ __global__ void __launch_bounds__(512) k_near_cell(
         }
         __syncthreads();
     }
-    for (int idx = tid; idx < npairs * t; idx += bd) {
-        const int p = idx / t, e = idx - p * t;
-        const int pk = pairs[p], j = pk & 0xFFFF, l = pk >> 16;
-        U[(((size_t)ch * nk + (size_t)cell * Ndiv + j) * 8 + l) * t + e] = Ua[idx];
+    if (r_st < rows_per_pass) {
+        for (int p = r_st; p < npairs; p += rows_per_pass) {
+            const int pk = pcache[p], j = pk & 0xFFFF, l = pk >> 16;
+            U[(((size_t)ch * nk + (size_t)cell * Ndiv + j) * 8 + l) * t + e_st] = Ua[p * tp + e_st];
+        }
+    }
+}
+
+// Register-blocked variant of k_near_cell for FP32 and compile-time band
+// counts: one thread owns one active (target, corner) pair p and keeps its
+// u block (NV x NC) in registers; per slot it forms the rows of
+// T = [y1 - h_head(q_coarse) z] Hc^T one at a time and adds Hv T.  Phases (a)
+// and (b) are those of k_near_cell.  Needs npairs <= blockDim.
+template <int NV, int NC>
+__global__ void __launch_bounds__(512) k_near_cell_rb(
+    const float2* __restrict__ X, const int* __restrict__ clist, const int* __restrict__ cstart,
+    const int* __restrict__ pairs, int npairs, const float* __restrict__ hd, int n_near,
+    const float2* __restrict__ Hv, const float2* __restrict__ Hc, const float* __restrict__ hc,
+    int n, int nd, int smin, int ns1, int rmin, int nr1, float2* __restrict__ U) {
+    constexpr int t = NV * NC, tp = t + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Ndiv = nd * nd * nd, nslot = ns1 * ns1 * ns1, nrel = nr1 * nr1 * nr1;
+    const int nk = n * n * n * Ndiv;
+    const int cell = blockIdx.x, ch = blockIdx.y;
+    float2* Xb = reinterpret_cast<float2*>(smem_raw);     // [npairs][tp]
+    float2* Y1 = Xb + (size_t)npairs * tp;                 // [Ndiv][tp]
+    float2* Zs = Y1 + (size_t)Ndiv * tp;                   // [Ndiv][tp]
+    float2* Hvs = Zs + (size_t)Ndiv * tp;                  // [8][NV*NV]
+    float2* Hcs = Hvs + 8 * NV * NV;                       // [8][NC*NC]
+    float* hcs = reinterpret_cast<float*>(Hcs + 8 * NC * NC);
+    float* hds = hcs + 8;
+    int* pcache = reinterpret_cast<int*>(hds + n_near);
+    int* scell = pcache + npairs;
+    const Int3 ci = unflat3(cell, n);
+    const float2* Xc = X + (size_t)ch * nk * 8 * t;
+    const int tid = threadIdx.x, bd = blockDim.x;
+    for (int i = tid; i < n_near; i += bd) hds[i] = hd[i];
+    for (int i = tid; i < npairs; i += bd) pcache[i] = pairs[i];
+    for (int i = tid; i < nslot * 8; i += bd) {
+        const int s = i >> 3, l = i & 7;
+        const Int3 so = unflat3(s, ns1);
+        scell[i] = flat3(ci.a + so.a + smin - ((l >> 2) & 1), ci.b + so.b + smin - ((l >> 1) & 1),
+                         ci.c + so.c + smin - (l & 1), n);
+    }
+    const int rows_per_pass = bd / t;
+    const int e_st = tid % t, r_st = tid / t;
+    const bool own = tid < npairs;
+    int jo = 0, lo = 0;
+    float2 u[NV][NC];
+#pragma unroll
+    for (int a = 0; a < NV; ++a)
+#pragma unroll
+        for (int b = 0; b < NC; ++b) u[a][b] = make_float2(0.f, 0.f);
+    __syncthreads();
+    if (own) { const int pk = pcache[tid]; jo = pk & 0xFFFF; lo = pk >> 16; }
+    for (int s = 0; s < nslot; ++s) {
+        const Int3 so = unflat3(s, ns1);
+        const int oa = so.a + smin, ob = so.b + smin, oc = so.c + smin;
+        if (r_st < rows_per_pass) {
+            for (int p = r_st; p < npairs; p += rows_per_pass) {
+                const int pk = pcache[p], js = pk & 0xFFFF, l = pk >> 16;
+                Xb[p * tp + e_st] = Xc[(((size_t)scell[s * 8 + l] * Ndiv + js) * 8 + l) * t + e_st];
+            }
+        }
+        for (int idx = tid; idx < 8 * (NV * NV + NC * NC + 1); idx += bd) {
+            const int l = idx & 7, q = idx >> 3;
+            const int l1 = (l >> 2) & 1, l2 = (l >> 1) & 1, l3 = l & 1;
+            const int kt = flat3(ci.a + l1, ci.b + l2, ci.c + l3, n);
+            const int r = ((oa - l1 - rmin) * nr1 + (ob - l2 - rmin)) * nr1 + (oc - l3 - rmin);
+            if (q < NV * NV) Hvs[l * NV * NV + q] = Hv[((size_t)kt * nrel + r) * NV * NV + q];
+            else if (q < NV * NV + NC * NC) Hcs[l * NC * NC + (q - NV * NV)] = Hc[((size_t)kt * nrel + r) * NC * NC + (q - NV * NV)];
+            else hcs[l] = hc[r];
+        }
+        __syncthreads();
+        const int* cs = cstart + s;
+        if (r_st < rows_per_pass) {
+            for (int j = r_st; j < Ndiv; j += rows_per_pass) {
+                float2 y = make_float2(0.f, 0.f), z = make_float2(0.f, 0.f);
+                const int q1 = cs[(size_t)j * (nslot + 1) + 1];
+                for (int q = cs[(size_t)j * (nslot + 1)]; q < q1; ++q) {
+                    const int en = clist[q];
+                    const float2 xv = Xb[(en & 0xFFFF) * tp + e_st];
+                    const float h = hds[en >> 16];
+                    y.x = fmaf(h, xv.x, y.x);
+                    y.y = fmaf(h, xv.y, y.y);
+                    z.x += xv.x;
+                    z.y += xv.y;
+                }
+                Y1[j * tp + e_st] = y;
+                Zs[j * tp + e_st] = z;
+            }
+        }
+        __syncthreads();
+        if (own) {
+            const float hcl = hcs[lo];
+            const float2* hcm = Hcs + lo * NC * NC;
+            const float2* hvm = Hvs + lo * NV * NV;
+            const float2* yr = Y1 + jo * tp;
+            const float2* zr = Zs + jo * tp;
+#pragma unroll
+            for (int n3 = 0; n3 < NV; ++n3) {
+                float2 g[NC];
+#pragma unroll
+                for (int n4 = 0; n4 < NC; ++n4) {
+                    const float2 yv = yr[n3 * NC + n4], zv = zr[n3 * NC + n4];
+                    g[n4] = make_float2(fmaf(-hcl, zv.x, yv.x), fmaf(-hcl, zv.y, yv.y));
+                }
+                float2 tr[NC];
+#pragma unroll
+                for (int n2 = 0; n2 < NC; ++n2) {
+                    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int n4 = 0; n4 < NC; ++n4) {
+                        const float2 h = hcm[n2 * NC + n4];
+                        acc.x = fmaf(g[n4].x, h.x, fmaf(-g[n4].y, h.y, acc.x));
+                        acc.y = fmaf(g[n4].x, h.y, fmaf(g[n4].y, h.x, acc.y));
+                    }
+                    tr[n2] = acc;
+                }
+#pragma unroll
+                for (int n1 = 0; n1 < NV; ++n1) {
+                    const float2 h = hvm[n1 * NV + n3];
+#pragma unroll
+                    for (int n2 = 0; n2 < NC; ++n2) {
+                        u[n1][n2].x = fmaf(h.x, tr[n2].x, fmaf(-h.y, tr[n2].y, u[n1][n2].x));
+                        u[n1][n2].y = fmaf(h.x, tr[n2].y, fmaf(h.y, tr[n2].x, u[n1][n2].y));
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (own) {
+        float2* dst = U + (((size_t)ch * nk + (size_t)cell * Ndiv + jo) * 8 + lo) * t;
+#pragma unroll
+        for (int a = 0; a < NV; ++a)
+#pragma unroll
+            for (int b = 0; b < NC; ++b) dst[a * NC + b] = u[a][b];
     }
 }
 
@@ -336,54 +725,86 @@ __global__ void __launch_bounds__(BSE_VEC_THREADS) k_prolong(
     const T* __restrict__ dE, const typename Cx<T>::V* __restrict__ psi, int n, int nd, int nv, int nc,
     int nb1, int nchains, int N, int Nc, typename Cx<T>::V* __restrict__ W, double2* __restrict__ part) {
     using V = typename Cx<T>::V;
-    __shared__ double2 red[BSE_MAX_CHAINS][BSE_VEC_THREADS];
+    // per-warp staging: M = R(k~_l) + u(k, l) for all chains, Dv, Dc of one
+    // (dense point, corner) pair; reused at the end for the block reduction
+    constexpr int WS = BSE_MAX_CHAINS * BSE_MAX_T + 2 * BSE_MAX_T;
+    constexpr int NW = BSE_VEC_THREADS / 32;
+    __shared__ __align__(16) unsigned char smraw[NW * WS * sizeof(double2)];
     const int t = nv * nc;
     const int Ndiv = nd * nd * nd;
     const int nk = N / t;
     const T inv_ndiv = (T)1 / (T)Ndiv;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    V* wm = reinterpret_cast<V*>(smraw) + warp * WS;
+    V* wdv = wm + BSE_MAX_CHAINS * BSE_MAX_T;
+    V* wdc = wdv + BSE_MAX_T;
+    int vq[2], cq[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) { const int e = lane + 32 * q; vq[q] = e / nc; cq[q] = e % nc; }
     double2 dot[BSE_MAX_CHAINS];
 #pragma unroll
     for (int ch = 0; ch < BSE_MAX_CHAINS; ++ch) dot[ch] = make_double2(0.0, 0.0);
-    for (int gid = blockIdx.x * blockDim.x + threadIdx.x; gid < N; gid += gridDim.x * blockDim.x) {
-        const int kd = gid / t, e = gid % t, v = e / nc, c = e % nc;
+    for (int kd = blockIdx.x * NW + warp; kd < nk; kd += gridDim.x * NW) {
         const int cell = kd / Ndiv, js = kd % Ndiv;
         const Int3 ci = unflat3(cell, n);
-        V acc[BSE_MAX_CHAINS];
+        V acc[BSE_MAX_CHAINS][2];
 #pragma unroll
-        for (int ch = 0; ch < BSE_MAX_CHAINS; ++ch) acc[ch] = czero<V>();
+        for (int ch = 0; ch < BSE_MAX_CHAINS; ++ch) { acc[ch][0] = czero<V>(); acc[ch][1] = czero<V>(); }
         for (int l = 0; l < 8; ++l) {
             const T f = (T)interp_weight(js, l, nd, nb1);
-            if (f == (T)0) continue;
+            if (f == (T)0) continue;                               // warp-uniform
             const int cc = flat3(ci.a + ((l >> 2) & 1), ci.b + ((l >> 1) & 1), ci.c + (l & 1), n);
             const V* dv = Dv + ((size_t)kd * 8 + l) * nv * nv;
             const V* dc = Dc + ((size_t)kd * 8 + l) * nc * nc;
-            for (int n1 = 0; n1 < nv; ++n1) {
-                const V a = cscale(dv[n1 * nv + v], f);
-                for (int n2 = 0; n2 < nc; ++n2) {
-                    const V wgt = cmul(a, conjg(dc[n2 * nc + c]));
-                    const int q = n1 * nc + n2;
+            for (int ch = 0; ch < nchains; ++ch)
+                for (int e = lane; e < t; e += 32) {
+                    V r = R[(size_t)ch * Nc + (size_t)cc * t + e];
+                    if (NEAR) r = cadd(r, Unf[(((size_t)ch * nk + kd) * 8 + l) * t + e]);
+                    wm[ch * BSE_MAX_T + e] = r;
+                }
+            for (int e = lane; e < nv * nv; e += 32) wdv[e] = dv[e];
+            for (int e = lane; e < nc * nc; e += 32) wdc[e] = dc[e];
+            __syncwarp();
 #pragma unroll
-                    for (int ch = 0; ch < BSE_MAX_CHAINS; ++ch) {
-                        if (ch >= nchains) break;
-                        V r = R[(size_t)ch * Nc + (size_t)cc * t + q];
-                        if (NEAR) r = cadd(r, Unf[(((size_t)ch * nk + kd) * 8 + l) * t + q]);
-                        acc[ch] = cadd(acc[ch], cmul(wgt, r));
+            for (int q = 0; q < 2; ++q) {
+                const int e = lane + 32 * q;
+                if (e >= t) break;
+                const int v = vq[q], c = cq[q];
+#pragma unroll
+                for (int ch = 0; ch < BSE_MAX_CHAINS; ++ch) {
+                    if (ch >= nchains) break;
+                    const V* m = wm + ch * BSE_MAX_T;
+                    V s = czero<V>();
+                    for (int n1 = 0; n1 < nv; ++n1) {
+                        V inner = czero<V>();
+                        for (int n2 = 0; n2 < nc; ++n2) inner = cadd(inner, cmul(m[n1 * nc + n2], conjg(wdc[n2 * nc + c])));
+                        s = cadd(s, cmul(wdv[n1 * nv + v], inner));
                     }
+                    acc[ch][q] = cadd(acc[ch][q], cscale(s, f));
                 }
             }
+            __syncwarp();
         }
-        const T de = dE[gid];
 #pragma unroll
-        for (int ch = 0; ch < BSE_MAX_CHAINS; ++ch) {
-            if (ch >= nchains) break;
-            const V p = psi[(size_t)ch * N + gid];
-            const V w = cadd(cscale(p, de), cscale(acc[ch], inv_ndiv));
-            W[(size_t)ch * N + gid] = w;
-            const double2 pd = to_d2(p), wd = to_d2(w);
-            dot[ch].x += pd.x * wd.x + pd.y * wd.y;
-            dot[ch].y += pd.x * wd.y - pd.y * wd.x;
+        for (int q = 0; q < 2; ++q) {
+            const int e = lane + 32 * q;
+            if (e >= t) break;
+            const size_t gid = (size_t)kd * t + e;
+            const T de = dE[gid];
+#pragma unroll
+            for (int ch = 0; ch < BSE_MAX_CHAINS; ++ch) {
+                if (ch >= nchains) break;
+                const V p = psi[(size_t)ch * N + gid];
+                const V w = cadd(cscale(p, de), cscale(acc[ch][q], inv_ndiv));
+                W[(size_t)ch * N + gid] = w;
+                const double2 pd = to_d2(p), wd = to_d2(w);
+                dot[ch].x += pd.x * wd.x + pd.y * wd.y;
+                dot[ch].y += pd.x * wd.y - pd.y * wd.x;
+            }
         }
     }
+    __syncthreads();
+    double2 (*red)[BSE_VEC_THREADS] = reinterpret_cast<double2 (*)[BSE_VEC_THREADS]>(smraw);
     for (int ch = 0; ch < nchains; ++ch) red[ch][threadIdx.x] = dot[ch];
     __syncthreads();
     for (int s = BSE_VEC_THREADS / 2; s > 0; s >>= 1) {
@@ -622,6 +1043,80 @@ inline int vec_blocks(long long N) {
     return (int)std::min<long long>(std::max<long long>(b, 1), BSE_MAX_VEC_BLOCKS);
 }
 
+// Restrict: register-blocked FP32 kernel for 3x3 and 4x4 bands, generic otherwise.
+template <typename T>
+void launch_restrict(bse_ctx* ctx, const bse_interp* s, int nchains, const void* psi, void* Q, __nv_bfloat16* bop,
+                     void* X) {
+    using V = typename Cx<T>::V;
+    const bse_coarse* c = s->co;
+    cudaStream_t st = ctx->stream;
+    const bool bf = c->kc_prec == BSE_PREC_BF16;
+    if constexpr (std::is_same<T, float>::value) {
+        const float2* p = (const float2*)psi;
+        const float2* dv = (const float2*)s->d_Dv;
+        const float2* dc = (const float2*)s->d_Dc;
+#define BSE_RB_RESTRICT(NV_, NC_)                                                                                   \
+    if (s->nv == NV_ && s->nc == NC_) {                                                                             \
+        if (bf)                                                                                                     \
+            k_restrict_rb<NV_, NC_, true><<<c->nkc, 256, 0, st>>>(p, dv, dc, s->n, s->nd, s->nb1, nchains, s->N,   \
+                                                                 c->Nc, nullptr, bop, c->ldk, (float2*)X);          \
+        else                                                                                                        \
+            k_restrict_rb<NV_, NC_, false><<<c->nkc, 256, 0, st>>>(p, dv, dc, s->n, s->nd, s->nb1, nchains, s->N,  \
+                                                                  c->Nc, (float2*)Q, nullptr, 0, (float2*)X);       \
+        return;                                                                                                     \
+    }
+        BSE_RB_RESTRICT(3, 3)
+        BSE_RB_RESTRICT(4, 4)
+#undef BSE_RB_RESTRICT
+    }
+    if (bf)
+        k_restrict<T, true><<<c->nkc, 256, 0, st>>>((const V*)psi, (const V*)s->d_Dv, (const V*)s->d_Dc, s->n, s->nd,
+                                                   s->nv, s->nc, s->nb1, nchains, s->N, c->Nc, nullptr, bop, c->ldk,
+                                                   (V*)X, nullptr);
+    else
+        k_restrict<T, false><<<c->nkc, 256, 0, st>>>((const V*)psi, (const V*)s->d_Dv, (const V*)s->d_Dc, s->n, s->nd,
+                                                    s->nv, s->nc, s->nb1, nchains, s->N, c->Nc, (V*)Q, nullptr, 0,
+                                                    (V*)X, nullptr);
+}
+
+// Prolong + diagonal: register-blocked FP32 kernel for 3x3, 4x4, 4x6 bands, generic otherwise.
+template <typename T>
+void launch_prolong(bse_ctx* ctx, const bse_interp* s, int nchains, const void* R, const void* U, const void* psi,
+                    void* W, double2* dot) {
+    using V = typename Cx<T>::V;
+    const bse_coarse* c = s->co;
+    cudaStream_t st = ctx->stream;
+    const int nb = vec_blocks(s->N);
+    const bool m3 = U != nullptr;
+    if constexpr (std::is_same<T, float>::value) {
+#define BSE_RB_PROLONG(NV_, NC_)                                                                                     \
+    if (s->nv == NV_ && s->nc == NC_) {                                                                              \
+        if (m3)                                                                                                      \
+            k_prolong_rb<NV_, NC_, true><<<nb, BSE_VEC_THREADS, 0, st>>>(                                            \
+                (const float2*)R, (const float2*)U, (const float2*)s->d_Dv, (const float2*)s->d_Dc,                  \
+                (const float*)s->d_dE, (const float2*)psi, s->n, s->nd, s->nb1, nchains, s->N, c->Nc, (float2*)W,    \
+                dot);                                                                                                \
+        else                                                                                                         \
+            k_prolong_rb<NV_, NC_, false><<<nb, BSE_VEC_THREADS, 0, st>>>(                                           \
+                (const float2*)R, nullptr, (const float2*)s->d_Dv, (const float2*)s->d_Dc, (const float*)s->d_dE,    \
+                (const float2*)psi, s->n, s->nd, s->nb1, nchains, s->N, c->Nc, (float2*)W, dot);                     \
+        return;                                                                                                      \
+    }
+        BSE_RB_PROLONG(3, 3)
+        BSE_RB_PROLONG(4, 4)
+        BSE_RB_PROLONG(4, 6)
+#undef BSE_RB_PROLONG
+    }
+    if (m3)
+        k_prolong<T, true><<<nb, BSE_VEC_THREADS, 0, st>>>((const V*)R, (const V*)U, (const V*)s->d_Dv,
+                                                          (const V*)s->d_Dc, (const T*)s->d_dE, (const V*)psi, s->n,
+                                                          s->nd, s->nv, s->nc, s->nb1, nchains, s->N, c->Nc, (V*)W, dot);
+    else
+        k_prolong<T, false><<<nb, BSE_VEC_THREADS, 0, st>>>((const V*)R, nullptr, (const V*)s->d_Dv,
+                                                           (const V*)s->d_Dc, (const T*)s->d_dE, (const V*)psi, s->n,
+                                                           s->nd, s->nv, s->nc, s->nb1, nchains, s->N, c->Nc, (V*)W, dot);
+}
+
 struct Timer {
     bse_ctx* ctx;
     bool on;
@@ -661,12 +1156,7 @@ int apply_h_typed(bse_ctx* ctx, bse_interp* s, int nchains, const void* psi_v, v
     V* X = m3 ? (V*)s->d_X : nullptr;
     {
         Timer tm(ctx, prof, KC_RESTRICT);
-        if (c->kc_prec == BSE_PREC_BF16)
-            k_restrict<T, true><<<c->nkc, 256, 0, st>>>(psi, (const V*)s->d_Dv, (const V*)s->d_Dc, s->n, s->nd, s->nv, s->nc,
-                                                       s->nb1, nchains, s->N, c->Nc, nullptr, s->d_Bop, c->ldk, X, s->d_stop);
-        else
-            k_restrict<T, false><<<c->nkc, 256, 0, st>>>(psi, (const V*)s->d_Dv, (const V*)s->d_Dc, s->n, s->nd, s->nv, s->nc,
-                                                        s->nb1, nchains, s->N, c->Nc, (V*)s->d_Q, nullptr, 0, X, s->d_stop);
+        launch_restrict<T>(ctx, s, nchains, psi, s->d_Q, s->d_Bop, X);
     }
     {
         Timer tm(ctx, prof, KC_KCAPPLY);
@@ -684,15 +1174,7 @@ int apply_h_typed(bse_ctx* ctx, bse_interp* s, int nchains, const void* psi_v, v
     }
     {
         Timer tm(ctx, prof, KC_PROLONG);
-        const int nb = vec_blocks(s->N);
-        if (m3)
-            k_prolong<T, true><<<nb, BSE_VEC_THREADS, 0, st>>>((const V*)s->d_R, (const V*)s->d_U, (const V*)s->d_Dv,
-                                                              (const V*)s->d_Dc, (const T*)s->d_dE, psi, s->n, s->nd, s->nv,
-                                                              s->nc, s->nb1, nchains, s->N, c->Nc, W, s->d_part_dot);
-        else
-            k_prolong<T, false><<<nb, BSE_VEC_THREADS, 0, st>>>((const V*)s->d_R, nullptr, (const V*)s->d_Dv,
-                                                               (const V*)s->d_Dc, (const T*)s->d_dE, psi, s->n, s->nd, s->nv,
-                                                               s->nc, s->nb1, nchains, s->N, c->Nc, W, s->d_part_dot);
+        launch_prolong<T>(ctx, s, nchains, s->d_R, m3 ? s->d_U : nullptr, psi, W, s->d_part_dot);
     }
     return BSE_OK;
 }
@@ -927,28 +1409,18 @@ int apply_scratch_typed(bse_ctx* ctx, const bse_interp* s, int nchains, const vo
     V* X = m3 ? (V*)sc.X : nullptr;
     if (c->kc_prec == BSE_PREC_BF16) {
         BSE_CUDA_TRY(ctx, cudaMemsetAsync(sc.bop, 0, sizeof(__nv_bfloat16) * 16 * (size_t)c->ldk, st));
-        k_restrict<T, true><<<c->nkc, 256, 0, st>>>(psi, (const V*)s->d_Dv, (const V*)s->d_Dc, s->n, s->nd, s->nv, s->nc,
-                                                   s->nb1, nchains, s->N, c->Nc, nullptr, sc.bop, c->ldk, X, nullptr);
+        launch_restrict<T>(ctx, s, nchains, psi, nullptr, sc.bop, X);
         int rc = bse_tc_apply_scratch(ctx, s, nchains, sc.bop, sc.part, sc.R);
         if (rc != BSE_OK) return rc;
     } else {
-        k_restrict<T, false><<<c->nkc, 256, 0, st>>>(psi, (const V*)s->d_Dv, (const V*)s->d_Dc, s->n, s->nd, s->nv, s->nc,
-                                                    s->nb1, nchains, s->N, c->Nc, (V*)sc.Q, nullptr, 0, X, nullptr);
+        launch_restrict<T>(ctx, s, nchains, psi, sc.Q, nullptr, X);
         k_kc_apply_simt<T><<<(c->Nc + 7) / 8, 256, 0, st>>>((const V*)c->d_kc, (const V*)sc.Q, c->Nc, nchains, (V*)sc.R);
     }
     if (m3) {
         int rc = bse_launch_near_field(ctx, s, nchains, X, sc.U);
         if (rc != BSE_OK) return rc;
     }
-    const int nb = vec_blocks(s->N);
-    if (m3)
-        k_prolong<T, true><<<nb, BSE_VEC_THREADS, 0, st>>>((const V*)sc.R, (const V*)sc.U, (const V*)s->d_Dv,
-                                                          (const V*)s->d_Dc, (const T*)s->d_dE, psi, s->n, s->nd, s->nv,
-                                                          s->nc, s->nb1, nchains, s->N, c->Nc, W, sc.dot);
-    else
-        k_prolong<T, false><<<nb, BSE_VEC_THREADS, 0, st>>>((const V*)sc.R, nullptr, (const V*)s->d_Dv,
-                                                           (const V*)s->d_Dc, (const T*)s->d_dE, psi, s->n, s->nd, s->nv,
-                                                           s->nc, s->nb1, nchains, s->N, c->Nc, W, sc.dot);
+    launch_prolong<T>(ctx, s, nchains, sc.R, m3 ? sc.U : nullptr, psi, W, sc.dot);
     return BSE_OK;
 }
 
@@ -974,9 +1446,29 @@ int launch_near_cell(bse_ctx* ctx, const bse_interp* s, int nchains, const void*
     return BSE_OK;
 }
 
+template <int NV, int NC>
+int launch_near_rb(bse_ctx* ctx, const bse_interp* s, int nchains, const void* X, void* U) {
+    const int smem = (int)s->cell_smem;      // the generic layout's size bounds this kernel's
+    if (smem > 48 * 1024)
+        BSE_CUDA_TRY(ctx, cudaFuncSetAttribute(k_near_cell_rb<NV, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    dim3 grid(s->co->nkc, nchains);
+    k_near_cell_rb<NV, NC><<<grid, 512, smem, ctx->stream>>>(
+        (const float2*)X, s->d_clist, s->d_cstart, s->d_pairs, s->npairs, (const float*)s->d_hd, s->n_near,
+        (const float2*)s->d_Hv, (const float2*)s->d_Hc, (const float*)s->d_hc, s->n, s->nd, s->smin, s->ns1, s->rmin,
+        s->nr1, (float2*)U);
+    return BSE_OK;
+}
+
 template <typename T>
 int launch_near_typed(bse_ctx* ctx, const bse_interp* s, int nchains, const void* X, void* U) {
     using V = typename Cx<T>::V;
+    if constexpr (std::is_same<T, float>::value) {
+        if (s->cell_smem && s->npairs <= 512) {
+            if (s->nv == 3 && s->nc == 3) return launch_near_rb<3, 3>(ctx, s, nchains, X, U);
+            if (s->nv == 4 && s->nc == 4) return launch_near_rb<4, 4>(ctx, s, nchains, X, U);
+            if (s->nv == 4 && s->nc == 6) return launch_near_rb<4, 6>(ctx, s, nchains, X, U);
+        }
+    }
     if (s->cell_smem) {
         if (s->nv <= 1) return launch_near_cell<T, 1>(ctx, s, nchains, X, U);
         if (s->nv <= 2) return launch_near_cell<T, 2>(ctx, s, nchains, X, U);

@@ -506,9 +506,10 @@ int setup_interp_typed(bse_ctx* ctx, bse_interp* s) {
         // (js', corner) pair index, so one coarse cell's targets share a slot's
         // source rows staged in shared memory.
         {
+            // corner-major order: neighbouring threads share a corner's head blocks
             std::vector<int> pairs, pidx((size_t)Ndiv * 8, -1);
-            for (int js = 0; js < Ndiv; ++js)
-                for (int l = 0; l < 8; ++l)
+            for (int l = 0; l < 8; ++l)
+                for (int js = 0; js < Ndiv; ++js)
                     if (interp_weight(js, l, nd, s->nb1) != 0.0) {
                         pidx[(size_t)js * 8 + l] = (int)pairs.size();
                         pairs.push_back(js | (l << 16));
@@ -524,8 +525,9 @@ int setup_interp_typed(bse_ctx* ctx, bse_interp* s) {
                 cstart[(size_t)js * (s->nslot + 1) + s->nslot] = (int)clist.size();
             }
             const size_t vs = sizeof(V), ts = sizeof(T);
-            const size_t smem = vs * (2 * (size_t)s->npairs * t + 2 * (size_t)Ndiv * t + 8 * (nv * nv + nc * nc)) +
-                                ts * (8 + (size_t)s->n_near);
+            const size_t tp = t + 1;                   // padded row stride (bank spread)
+            const size_t smem = vs * (2 * (size_t)s->npairs * tp + 2 * (size_t)Ndiv * tp + 8 * (nv * nv + nc * nc)) +
+                                ts * (8 + (size_t)s->n_near) + sizeof(int) * ((size_t)s->npairs + 8 * (size_t)s->nslot);
             int maxsm = 0;
             cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
             const bool fits = s->n_near < 65536 && s->npairs < 65536 && smem + 1024 <= (size_t)maxsm;

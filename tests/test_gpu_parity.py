@@ -107,6 +107,20 @@ def test_apply_h_f64_matches_oracle(ctx, case):
     co.free()
 
 
+@pytest.mark.parametrize("nv,nc,method", [(4, 4, "m3"), (4, 6, "m3"), (3, 3, "m3"), (2, 3, "m3"), (4, 4, "m1")])
+def test_apply_h_fp32_matches_oracle(ctx, nv, nc, method):
+    """FP32 vectors with complex64 K_c (register-blocked kernels for 3x3, 4x4
+    and 4x6 bands, generic ones otherwise), 3 chains: FP32-level agreement."""
+    co, it = gpu_system(ctx, 13, nv, nc, 3, 2, method, kc_prec=1, vec_prec=1)
+    H = oracle_H(13, nv, nc, 3, 2, method)
+    x = synth.random_vectors(9, (3, it.N)).astype(np.complex64).astype(np.complex128)
+    y = apply_gpu(ctx, it, x)
+    yr = (H @ x.T).T
+    assert np.abs(y - yr).max() <= 2e-5 * np.abs(yr).max()
+    it.free()
+    co.free()
+
+
 # ----------------------------------------------------------- Haydock FP64
 @pytest.mark.parametrize("method", ["m1", "m3"])
 def test_haydock_fp64_matches_oracle(ctx, method):
