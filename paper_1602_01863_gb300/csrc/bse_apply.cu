@@ -587,7 +587,7 @@ __global__ void __launch_bounds__(512) k_near_cell(
 // u block (NV x NC) in registers; per slot it forms the rows of
 // T = [y1 - h_head(q_coarse) z] Hc^T one at a time and adds Hv T.  Phases (a)
 // and (b) are those of k_near_cell.  Needs npairs <= blockDim.
-template <int NV, int NC>
+template <int NV, int NC, int PF>
 __global__ void __launch_bounds__(512) k_near_cell_rb(
     const float2* __restrict__ X, const int* __restrict__ clist, const int* __restrict__ cstart,
     const int* __restrict__ pairs, int npairs, const float* __restrict__ hd, int n_near,
@@ -629,13 +629,37 @@ __global__ void __launch_bounds__(512) k_near_cell_rb(
         for (int b = 0; b < NC; ++b) u[a][b] = make_float2(0.f, 0.f);
     __syncthreads();
     if (own) { const int pk = pcache[tid]; jo = pk & 0xFFFF; lo = pk >> 16; }
+    // PF > 0: the next slot's source rows are loaded into registers while the
+    // current slot computes (PF >= rows per thread, checked by the launcher).
+    float2 pf[PF > 0 ? PF : 1];
+    auto fetch = [&](int s_) {
+        if (r_st < rows_per_pass) {
+#pragma unroll
+            for (int k = 0; k < PF; ++k) {
+                const int p = r_st + k * rows_per_pass;
+                if (p < npairs) {
+                    const int pk = pcache[p], js = pk & 0xFFFF, l = pk >> 16;
+                    pf[k] = Xc[(((size_t)scell[s_ * 8 + l] * Ndiv + js) * 8 + l) * t + e_st];
+                }
+            }
+        }
+    };
+    if (PF > 0) fetch(0);
     for (int s = 0; s < nslot; ++s) {
         const Int3 so = unflat3(s, ns1);
         const int oa = so.a + smin, ob = so.b + smin, oc = so.c + smin;
         if (r_st < rows_per_pass) {
-            for (int p = r_st; p < npairs; p += rows_per_pass) {
-                const int pk = pcache[p], js = pk & 0xFFFF, l = pk >> 16;
-                Xb[p * tp + e_st] = Xc[(((size_t)scell[s * 8 + l] * Ndiv + js) * 8 + l) * t + e_st];
+            if (PF > 0) {
+#pragma unroll
+                for (int k = 0; k < PF; ++k) {
+                    const int p = r_st + k * rows_per_pass;
+                    if (p < npairs) Xb[p * tp + e_st] = pf[k];
+                }
+            } else {
+                for (int p = r_st; p < npairs; p += rows_per_pass) {
+                    const int pk = pcache[p], js = pk & 0xFFFF, l = pk >> 16;
+                    Xb[p * tp + e_st] = Xc[(((size_t)scell[s * 8 + l] * Ndiv + js) * 8 + l) * t + e_st];
+                }
             }
         }
         for (int idx = tid; idx < 8 * (NV * NV + NC * NC + 1); idx += bd) {
@@ -648,6 +672,7 @@ __global__ void __launch_bounds__(512) k_near_cell_rb(
             else hcs[l] = hc[r];
         }
         __syncthreads();
+        if (PF > 0 && s + 1 < nslot) fetch(s + 1);
         const int* cs = cstart + s;
         if (r_st < rows_per_pass) {
             for (int j = r_st; j < Ndiv; j += rows_per_pass) {
@@ -1446,13 +1471,16 @@ int launch_near_cell(bse_ctx* ctx, const bse_interp* s, int nchains, const void*
     return BSE_OK;
 }
 
-template <int NV, int NC>
+template <int NV, int NC, int PF>
 int launch_near_rb(bse_ctx* ctx, const bse_interp* s, int nchains, const void* X, void* U) {
-    const int smem = (int)s->cell_smem;      // the generic layout's size bounds this kernel's
+    constexpr int t = NV * NC, tp = t + 1;
+    const size_t bytes = sizeof(float2) * ((size_t)s->npairs * tp + 2 * (size_t)s->Ndiv * tp + 8 * (NV * NV + NC * NC)) +
+                         sizeof(float) * (8 + (size_t)s->n_near) + sizeof(int) * ((size_t)s->npairs + 8 * (size_t)s->nslot);
+    const int smem = (int)bytes;
     if (smem > 48 * 1024)
-        BSE_CUDA_TRY(ctx, cudaFuncSetAttribute(k_near_cell_rb<NV, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        BSE_CUDA_TRY(ctx, cudaFuncSetAttribute(k_near_cell_rb<NV, NC, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     dim3 grid(s->co->nkc, nchains);
-    k_near_cell_rb<NV, NC><<<grid, 512, smem, ctx->stream>>>(
+    k_near_cell_rb<NV, NC, PF><<<grid, 512, smem, ctx->stream>>>(
         (const float2*)X, s->d_clist, s->d_cstart, s->d_pairs, s->npairs, (const float*)s->d_hd, s->n_near,
         (const float2*)s->d_Hv, (const float2*)s->d_Hc, (const float*)s->d_hc, s->n, s->nd, s->smin, s->ns1, s->rmin,
         s->nr1, (float2*)U);
@@ -1464,9 +1492,13 @@ int launch_near_typed(bse_ctx* ctx, const bse_interp* s, int nchains, const void
     using V = typename Cx<T>::V;
     if constexpr (std::is_same<T, float>::value) {
         if (s->cell_smem && s->npairs <= 512) {
-            if (s->nv == 3 && s->nc == 3) return launch_near_rb<3, 3>(ctx, s, nchains, X, U);
-            if (s->nv == 4 && s->nc == 4) return launch_near_rb<4, 4>(ctx, s, nchains, X, U);
-            if (s->nv == 4 && s->nc == 6) return launch_near_rb<4, 6>(ctx, s, nchains, X, U);
+            // rows of the slot staging each of the 512 threads owns
+            const int rows = (s->npairs + 512 / s->t - 1) / (512 / s->t);
+            if (s->nv == 3 && s->nc == 3)
+                return rows <= 8 ? launch_near_rb<3, 3, 8>(ctx, s, nchains, X, U) : launch_near_rb<3, 3, 0>(ctx, s, nchains, X, U);
+            if (s->nv == 4 && s->nc == 4)
+                return rows <= 12 ? launch_near_rb<4, 4, 12>(ctx, s, nchains, X, U) : launch_near_rb<4, 4, 0>(ctx, s, nchains, X, U);
+            if (s->nv == 4 && s->nc == 6) return launch_near_rb<4, 6, 0>(ctx, s, nchains, X, U);
         }
     }
     if (s->cell_smem) {
