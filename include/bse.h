@@ -137,6 +137,9 @@ void bse_free_coarse(bse_coarse* coarse);
  * `vec_prec` (F64 or F32) is the precision of the Lanczos vectors and of the
  * restrict / prolong / near-field arithmetic; Lanczos reductions are FP64
  * in every mode.  The coarse handle must outlive the interp handle.
+ * With BF16 K_c the set-up autotunes the tensor-core apply: it times a few
+ * splits of the K_c stream over the SMs on this K_c and keeps the fastest
+ * (cached per shape for the process).
  * Errors: BSE_ERR_ARG (n_div < 1; M3 with width_w >= n / 2, where the near
  * region would wrap around the zone; bad flags), BSE_ERR_OOM, BSE_ERR_CUDA. */
 int bse_interp_setup(bse_ctx* ctx, const bse_coarse* coarse, int n_div, int scheme,
@@ -186,6 +189,10 @@ int bse_apply_h_noalloc(bse_ctx* ctx, bse_interp* interp, int nvec, const void* 
  *   b          [chains][nsteps + 1]   b_1 = 0, b_2 .. b_{m+1}
  *   pnorm2     [chains]               ||P||^2
  *   steps_done [chains]               m, or fewer after a breakdown
+ * With BSE_USE_GRAPH and nsys > 1 the whole batch is captured as one CUDA
+ * graph (each system's loop on its own branch, longest systems spread over up
+ * to 8 concurrent branches) and launched once; the results equal the
+ * systems run one by one.  Each handle may appear once (it owns the scratch).
  * flags: BSE_REORTH_CGS2, BSE_USE_GRAPH, BSE_PROFILE.  A chain whose
  * b_{i+1} < 1e-12 max|a| stops there (BSE_WARN_BREAKDOWN).  Device waits
  * are bounded; a wait that gives up returns BSE_ERR_TIMEOUT. */

@@ -231,7 +231,12 @@ int bse_haydock_run(bse_ctx* ctx, bse_interp* const* sys, int nsys, const int* n
         total += npol[i];
     }
     if (!finite_arr(pol_dirs, 3 * (size_t)total)) return set_arg_error(ctx, "non-finite direction");
+    for (int i = 0; i < nsys; ++i)
+        for (int j = 0; j < i; ++j)
+            if (sys[i] == sys[j]) return set_arg_error(ctx, "a system handle appears twice (each owns its scratch)");
     if (cudaSetDevice(ctx->device) != cudaSuccess) return BSE_ERR_CUDA;
+    if (nsys > 1 && (flags & BSE_USE_GRAPH) && !(flags & BSE_PROFILE))
+        return bse_run_batch(ctx, sys, nsys, npol, pol_dirs, nsteps, flags, a, b, pnorm2, steps_done);
     int worst = BSE_OK, off = 0;
     for (int i = 0; i < nsys; ++i) {
         int rc = bse_run_chains(ctx, sys[i], npol[i], pol_dirs + 3 * off, nsteps, flags, a + (size_t)off * nsteps,

@@ -1383,6 +1383,117 @@ int bse_run_chains(bse_ctx* ctx, bse_interp* s, int npol, const double* pol_dirs
     return run_chains_typed<float>(ctx, s, npol, pol_dirs, nsteps, flags, a, b, pnorm2, steps_done);
 }
 
+// Many independent systems in one CUDA graph: every system's whole Haydock
+// loop is captured on one of up to 8 side streams forked from the context
+// stream (longest systems first, each onto the least-loaded stream) and
+// joined back, so the batch is a single graph launch whose branches run
+// concurrently on the GPU.
+int bse_run_batch(bse_ctx* ctx, bse_interp* const* sys, int nsys, const int* npol, const double* pol_dirs, int m,
+                  int flags, double* a, double* b, double* pnorm2, int* steps_done) {
+    const bool reorth = flags & BSE_REORTH_CGS2;
+    cudaStream_t main_st = ctx->stream;
+    std::vector<double*> d_dirs(nsys, nullptr), d_pn2(nsys, nullptr);
+    std::vector<int> first(nsys);
+    int rc = BSE_OK, off = 0;
+    auto cleanup = [&]() {
+        for (int i = 0; i < nsys; ++i) { cudaFree(d_dirs[i]); cudaFree(d_pn2[i]); }
+    };
+    for (int i = 0; i < nsys; ++i) {
+        bse_interp* s = sys[i];
+        rc = (s->vec_prec == BSE_PREC_F64) ? ensure_state<double>(ctx, s, m, reorth) : ensure_state<float>(ctx, s, m, reorth);
+        if (rc == BSE_OK) rc = bse_alloc(ctx, (void**)&d_dirs[i], sizeof(double) * 3 * BSE_MAX_CHAINS, "directions");
+        if (rc == BSE_OK) rc = bse_alloc(ctx, (void**)&d_pn2[i], sizeof(double) * BSE_MAX_CHAINS, "norms");
+        if (rc != BSE_OK) { cleanup(); return rc; }
+        cudaMemcpyAsync(d_dirs[i], pol_dirs + 3 * off, sizeof(double) * 3 * npol[i], cudaMemcpyHostToDevice, main_st);
+        first[i] = off;
+        off += npol[i];
+    }
+    const int K = std::min(nsys, 8);
+    std::vector<cudaStream_t> side(K, nullptr);
+    std::vector<cudaEvent_t> join(K, nullptr);
+    cudaEvent_t fork = nullptr;
+    cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    for (int k = 0; k < K; ++k) {
+        cudaStreamCreateWithFlags(&side[k], cudaStreamNonBlocking);
+        cudaEventCreateWithFlags(&join[k], cudaEventDisableTiming);
+    }
+    std::vector<int> order(nsys);
+    std::vector<double> cost(nsys);
+    for (int i = 0; i < nsys; ++i) {
+        const bse_interp* s = sys[i];
+        order[i] = i;
+        cost[i] = (double)s->co->Nc * s->co->Nc * npol[i] + (double)s->N * npol[i] * 64.0 +
+                  (s->scheme == BSE_SCHEME_M3 ? (double)s->nk * s->npairs * s->t * npol[i] * 8.0 : 0.0);
+    }
+    std::sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(main_st, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaEventRecord(fork, main_st);
+        for (int k = 0; k < K; ++k) cudaStreamWaitEvent(side[k], fork, 0);
+        std::vector<double> load(K, 0.0);
+        for (int i : order) {
+            const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            load[k] += cost[i];
+            ctx->stream = side[k];
+            rc = (sys[i]->vec_prec == BSE_PREC_F64)
+                     ? enqueue_chains<double>(ctx, sys[i], npol[i], d_dirs[i], d_pn2[i], m, reorth, false)
+                     : enqueue_chains<float>(ctx, sys[i], npol[i], d_dirs[i], d_pn2[i], m, reorth, false);
+            ctx->stream = main_st;
+            if (rc != BSE_OK) break;
+        }
+        for (int k = 0; k < K; ++k) {
+            cudaEventRecord(join[k], side[k]);
+            cudaStreamWaitEvent(main_st, join[k], 0);
+        }
+        e = cudaStreamEndCapture(main_st, &g);
+    }
+    ctx->stream = main_st;
+    if (e == cudaSuccess && rc == BSE_OK) e = cudaGraphInstantiate(&ge, g, 0);
+    if (e == cudaSuccess && rc == BSE_OK) e = cudaGraphLaunch(ge, main_st);
+    std::vector<std::vector<int>> stop(nsys, std::vector<int>(BSE_MAX_CHAINS));
+    int status = 0;
+    if (e == cudaSuccess && rc == BSE_OK) {
+        for (int i = 0; i < nsys; ++i) {
+            const bse_interp* s = sys[i];
+            const int o = first[i];
+            cudaMemcpyAsync(pnorm2 + o, d_pn2[i], sizeof(double) * npol[i], cudaMemcpyDeviceToHost, main_st);
+            for (int ch = 0; ch < npol[i]; ++ch) {
+                cudaMemcpyAsync(a + (size_t)(o + ch) * m, s->d_a + (size_t)ch * m, sizeof(double) * m, cudaMemcpyDeviceToHost, main_st);
+                cudaMemcpyAsync(b + (size_t)(o + ch) * (m + 1), s->d_b + (size_t)ch * (m + 1), sizeof(double) * (m + 1),
+                                cudaMemcpyDeviceToHost, main_st);
+            }
+            cudaMemcpyAsync(stop[i].data(), s->d_stop, sizeof(int) * BSE_MAX_CHAINS, cudaMemcpyDeviceToHost, main_st);
+        }
+        cudaMemcpyAsync(&status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, main_st);
+        e = cudaStreamSynchronize(main_st);
+    }
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+    for (int k = 0; k < K; ++k) { cudaStreamDestroy(side[k]); cudaEventDestroy(join[k]); }
+    cudaEventDestroy(fork);
+    cleanup();
+    if (rc != BSE_OK) return rc;
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        ctx->err = std::string("batched Haydock graph: ") + cudaGetErrorString(e);
+        return BSE_ERR_CUDA;
+    }
+    if (status != 0) {
+        cudaMemset(ctx->d_status, 0, sizeof(int));
+        ctx->err = "a bounded device wait in the tensor-core K_c apply gave up";
+        return BSE_ERR_TIMEOUT;
+    }
+    int warn = BSE_OK;
+    for (int i = 0; i < nsys; ++i)
+        for (int ch = 0; ch < npol[i]; ++ch) {
+            steps_done[first[i] + ch] = stop[i][ch] ? stop[i][ch] : m;
+            if (stop[i][ch]) warn = BSE_WARN_BREAKDOWN;
+        }
+    return warn;
+}
+
 int bse_make_dipoles(bse_ctx* ctx, bse_interp* s, int npol, const double* pol_dirs, void* p_out, double* pnorm2) {
     if (s->vec_prec == BSE_PREC_F64) return dipoles_typed<double>(ctx, s, npol, pol_dirs, p_out, pnorm2);
     return dipoles_typed<float>(ctx, s, npol, pol_dirs, p_out, pnorm2);

@@ -191,6 +191,8 @@ int bse_setup_interp_device(bse_ctx* ctx, bse_interp* s);
 int bse_apply_once(bse_ctx* ctx, bse_interp* s, int nvec, const void* x, void* y, bool profile);
 int bse_run_chains(bse_ctx* ctx, bse_interp* s, int npol, const double* pol_dirs, int nsteps,
                    int flags, double* a, double* b, double* pnorm2, int* steps_done);
+int bse_run_batch(bse_ctx* ctx, bse_interp* const* sys, int nsys, const int* npol, const double* pol_dirs, int m,
+                  int flags, double* a, double* b, double* pnorm2, int* steps_done);
 int bse_make_dipoles(bse_ctx* ctx, bse_interp* s, int npol, const double* pol_dirs, void* p_out,
                      double* pnorm2);
 int bse_cf_device(bse_ctx* ctx, int nchains, int nsteps, const int* steps_done, const double* a,

@@ -23,6 +23,9 @@
 
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "bse_internal.cuh"
 
@@ -362,35 +365,111 @@ struct TcState {
 
 }  // namespace
 
+namespace {
+
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, int> g_tuned_ctas;     // (N_c, ldk, SM count) -> CTA count
+
+// Autotuner for the persistent split of the k-block sequence: times the
+// tensor-core apply (+ reduce) for a few CTA counts on the handle's own K_c
+// with CUDA events and keeps the fastest; the choice is cached per shape.
+int tune_ctas(bse_ctx* ctx, bse_interp* s, const CUtensorMap& mkr, const CUtensorMap& mki, const CUtensorMap& mb) {
+    const bse_coarse* c = s->co;
+    const auto key = std::make_tuple(c->Nc, c->ldk, ctx->sm_count);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tuned_ctas.find(key);
+        if (it != g_tuned_ctas.end()) return it->second;
+    }
+    const int sm = std::max(ctx->sm_count, 1);
+    const long long total = (long long)((c->Nc + BM - 1) / BM) * (c->ldk / BK);
+    std::vector<int> cand;
+    for (int d : {1, 2, 4, 8}) {
+        const int g = (int)std::min<long long>(std::max(sm / d, 1), total);
+        if (std::find(cand.begin(), cand.end(), g) == cand.end()) cand.push_back(g);
+    }
+    const int g34 = (int)std::min<long long>(std::max(3 * sm / 4, 1), total);
+    if (std::find(cand.begin(), cand.end(), g34) == cand.end()) cand.push_back(g34);
+    size_t part_bytes = 0;
+    for (int g : cand) {
+        const TcPlan p = plan_for(c->Nc, c->ldk, g);
+        part_bytes = std::max(part_bytes, sizeof(float) * (size_t)p.ctas * p.seg_max * BM * 32);
+    }
+    float* d_part = nullptr;
+    if (bse_alloc(ctx, (void**)&d_part, part_bytes, "autotune partials") != BSE_OK) return sm;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = cand[0];
+    float best_ms = 1e30f;
+    for (int g : cand) {
+        const TcPlan p = plan_for(c->Nc, c->ldk, g);
+        int* d_tc = nullptr;
+        long long* d_q = nullptr;
+        if (bse_alloc(ctx, (void**)&d_tc, sizeof(int) * p.tile_cta.size(), "autotune tables") != BSE_OK) continue;
+        if (bse_alloc(ctx, (void**)&d_q, sizeof(long long) * p.q0.size(), "autotune tables") != BSE_OK) { cudaFree(d_tc); continue; }
+        cudaMemcpy(d_tc, p.tile_cta.data(), sizeof(int) * p.tile_cta.size(), cudaMemcpyHostToDevice);
+        cudaMemcpy(d_q, p.q0.data(), sizeof(long long) * p.q0.size(), cudaMemcpyHostToDevice);
+        auto launch = [&]() {
+            k_tc_apply<<<p.ctas, TC_THREADS, STAGES * STAGE_BYTES + 1024, ctx->stream>>>(
+                mkr, mki, mb, p.kblocks_per_row, p.total, p.seg_max, d_part, ctx->d_status);
+            k_tc_reduce<<<(c->Nc + 127) / 128, 128, 0, ctx->stream>>>(d_part, d_tc, d_q, p.kblocks_per_row, p.seg_max,
+                                                                     c->Nc, 1, (float2*)s->d_R);
+        };
+        for (int r = 0; r < 3; ++r) launch();
+        cudaEventRecord(e0, ctx->stream);
+        const int reps = 10;
+        for (int r = 0; r < reps; ++r) launch();
+        cudaEventRecord(e1, ctx->stream);
+        float ms = 0.f;
+        if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms / reps < best_ms) {
+            best_ms = ms / reps;
+            best = g;
+        }
+        cudaFree(d_tc);
+        cudaFree(d_q);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(d_part);
+    cudaGetLastError();
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tuned_ctas[key] = best;
+    return best;
+}
+
+}  // namespace
+
 int bse_tc_prepare(bse_ctx* ctx, bse_interp* s) {
     const bse_coarse* c = s->co;
-    TcState* st = new TcState();
-    st->plan = plan_for(c->Nc, c->ldk, ctx->sm_count);
-    const TcPlan& p = st->plan;
     int rc;
-    if ((rc = bse_alloc(ctx, (void**)&s->d_Bop, sizeof(__nv_bfloat16) * BN * (size_t)c->ldk, "split-BF16 operand")) != BSE_OK ||
-        (rc = bse_alloc(ctx, (void**)&s->d_part, sizeof(float) * (size_t)p.ctas * p.seg_max * BM * 32, "tile partials")) != BSE_OK ||
+    if ((rc = bse_alloc(ctx, (void**)&s->d_Bop, sizeof(__nv_bfloat16) * BN * (size_t)c->ldk, "split-BF16 operand")) != BSE_OK)
+        return rc;
+    BSE_CUDA_TRY(ctx, cudaMemset(s->d_Bop, 0, sizeof(__nv_bfloat16) * BN * (size_t)c->ldk));
+    static bool attr_set = false;
+    if (!attr_set) {
+        BSE_CUDA_TRY(ctx, cudaFuncSetAttribute(k_tc_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, STAGES * STAGE_BYTES + 1024));
+        attr_set = true;
+    }
+    TcState* st = new TcState();
+    if ((rc = make_map(ctx, &st->map_kr, c->d_kr, c->ldk, c->Nc, BM)) != BSE_OK ||
+        (rc = make_map(ctx, &st->map_ki, c->d_ki, c->ldk, c->Nc, BM)) != BSE_OK ||
+        (rc = make_map(ctx, &st->map_b, s->d_Bop, c->ldk, BN, BN)) != BSE_OK) {
+        delete st;
+        return rc;
+    }
+    const int ctas = tune_ctas(ctx, s, st->map_kr, st->map_ki, st->map_b);
+    st->plan = plan_for(c->Nc, c->ldk, ctas);
+    const TcPlan& p = st->plan;
+    if ((rc = bse_alloc(ctx, (void**)&s->d_part, sizeof(float) * (size_t)p.ctas * p.seg_max * BM * 32, "tile partials")) != BSE_OK ||
         (rc = bse_alloc(ctx, (void**)&st->d_tile_cta, sizeof(int) * p.tile_cta.size(), "tile schedule")) != BSE_OK ||
         (rc = bse_alloc(ctx, (void**)&st->d_q0, sizeof(long long) * p.q0.size(), "cta schedule")) != BSE_OK) {
         cudaFree(st->d_tile_cta); cudaFree(st->d_q0);
         delete st;
         return rc;
     }
-    BSE_CUDA_TRY(ctx, cudaMemset(s->d_Bop, 0, sizeof(__nv_bfloat16) * BN * (size_t)c->ldk));
     BSE_CUDA_TRY(ctx, cudaMemcpy(st->d_tile_cta, p.tile_cta.data(), sizeof(int) * p.tile_cta.size(), cudaMemcpyHostToDevice));
     BSE_CUDA_TRY(ctx, cudaMemcpy(st->d_q0, p.q0.data(), sizeof(long long) * p.q0.size(), cudaMemcpyHostToDevice));
-    if ((rc = make_map(ctx, &st->map_kr, c->d_kr, c->ldk, c->Nc, BM)) != BSE_OK ||
-        (rc = make_map(ctx, &st->map_ki, c->d_ki, c->ldk, c->Nc, BM)) != BSE_OK ||
-        (rc = make_map(ctx, &st->map_b, s->d_Bop, c->ldk, BN, BN)) != BSE_OK) {
-        cudaFree(st->d_tile_cta); cudaFree(st->d_q0);
-        delete st;
-        return rc;
-    }
-    static bool attr_set = false;
-    if (!attr_set) {
-        BSE_CUDA_TRY(ctx, cudaFuncSetAttribute(k_tc_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, STAGES * STAGE_BYTES + 1024));
-        attr_set = true;
-    }
     s->tc_ctas = p.ctas;
     s->tc_kblocks = p.kblocks_per_row;
     s->tc_state = st;
