@@ -214,6 +214,59 @@ int bse_spectrum(bse_ctx* ctx, int nchains, int nsteps, const int* steps_done,
                  const double* a, const double* b, const double* pnorm2, double prefactor,
                  double eta, int nw, const double* omega, double* eps);
 
+/* ------------------------------------------------------------------------
+ * Learned near-diagonal residual.  Not in the paper: a small network
+ * predicts N_k (K_explicit - K_M1) for dense pairs closer than a radius, and
+ * its evaluation, as a Hermitian translation-invariant stencil, is added to
+ * the M1 Hamiltonian in place of the Method-3 treatment.  M1 without it stays
+ * the fallback and the reference its error is judged against.
+ *
+ * Network: d_in -> 128 -> 128 -> 128 -> 2, exact-erf GELU, BF16 weights,
+ * FP32 activations and accumulation, FP32 master weights and Adam state.
+ * Parameters (FP32, d_in = 6 + 2 t for a system with t transitions):
+ * W1 [128][d_in], b1 [128], W2 [128][128], b2, W3 [128][128], b3,
+ * W4 [2][128], b4 [2].  Inputs per (k, k', vc, v'c'): q (3, minimum image of
+ * k - k' on orthonormal axes), |q|, onehot(vc) [t], onehot(v'c') [t],
+ * dE_vc(k), dE_v'c'(k').  Device buffers X [batch][d_in], Y and out
+ * [batch][2] are FP32.                                                       */
+typedef struct bse_mlp bse_mlp;
+
+/* Number of FP32 parameters for input size d_in. */
+int bse_mlp_param_count(int d_in);
+/* Network with host initial parameters init_params [bse_mlp_param_count]
+ * (the caller draws them), able to process batches up to max_batch. */
+int bse_mlp_create(bse_ctx* ctx, int d_in, int max_batch, const float* init_params, bse_mlp** out);
+void bse_mlp_free(bse_mlp* mlp);
+/* Copy the FP32 master parameters to host. */
+int bse_mlp_get_params(bse_ctx* ctx, const bse_mlp* mlp, float* host_params);
+/* Inference with the BF16 weights: out [batch][2] (device). */
+int bse_mlp_forward(bse_ctx* ctx, bse_mlp* mlp, int batch, const float* X, float* out);
+/* Gradients of the loss mean_b sum_{re,im} (out - Y)^2 with respect to the
+ * parameters (host, FP32, parameter layout) and the loss; no update. */
+int bse_mlp_gradients(bse_ctx* ctx, bse_mlp* mlp, int batch, const float* X, const float* Y,
+                      float* grad_host, double* loss);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) on that
+ * loss with learning rate lr; *loss gets the loss before the step. */
+int bse_mlp_train_step(bse_ctx* ctx, bse_mlp* mlp, int batch, const float* X, const float* Y, float lr,
+                       double* loss);
+/* Training data from the method: for nblocks sampled dense pairs
+ * (host_kd[i], host_kd2[i]) of `interp` (complex128 or complex64 K_c,
+ * t <= 16), all t x t entries: features X [nblocks t^2][6 + 2t] and targets
+ * Y = N_k (K_explicit - K_M1) [nblocks t^2][2] (device), row order
+ * (pair, vc, v'c').  K_explicit is the model kernel on the dense mesh in FP64
+ * (Eqs. bse2-bse3b with the model); K_M1 = (1/N_div) F K_c F^H (Eq. interp1). */
+int bse_pairs_generate(bse_ctx* ctx, const bse_interp* interp, int nblocks, const int* host_kd,
+                       const int* host_kd2, float* X, float* Y);
+/* Evaluate `mlp` once over every dense offset delta with |delta| < radius
+ * (dense steps) and every band pair, with each dE input at its average over
+ * the dense mesh, symmetrise it to a Hermitian stencil T(delta) =
+ * [out(delta) + out(-delta)^H] / (2 N_k), and add (T * psi)(k) =
+ * sum_delta T(delta) psi(k - delta) (periodic convolution, computed with
+ * separable DFTs) to every H application of `interp` (an M1 handle).
+ * mlp = NULL switches the correction off.  Requires 1 <= radius <= L/2,
+ * L = n n_div. */
+int bse_interp_set_learned(bse_ctx* ctx, bse_interp* interp, bse_mlp* mlp, int radius);
+
 #ifdef __cplusplus
 }
 #endif

@@ -34,7 +34,9 @@ KERNEL_CLASSES = ("restrict", "kc_apply", "prolong", "near_field", "lanczos")
 EXPORTED = ("bse_version", "bse_ctx_create", "bse_ctx_destroy", "bse_last_error", "bse_build_coarse",
             "bse_coarse_get_kc", "bse_free_coarse", "bse_interp_setup", "bse_free_interp", "bse_interp_info",
             "bse_dipoles", "bse_apply_h", "bse_apply_h_noalloc", "bse_haydock_run", "bse_last_kernel_times",
-            "bse_spectrum")
+            "bse_spectrum", "bse_mlp_param_count", "bse_mlp_create", "bse_mlp_free", "bse_mlp_get_params",
+            "bse_mlp_forward", "bse_mlp_gradients", "bse_mlp_train_step", "bse_pairs_generate",
+            "bse_interp_set_learned")
 
 
 class BseError(RuntimeError):
@@ -89,6 +91,17 @@ def load(path: str | None = None):
     lib.bse_haydock_run.argtypes = [_P, C.POINTER(_P), C.c_int, _I, _D, C.c_int, C.c_int, _D, _D, _D, _I]
     lib.bse_last_kernel_times.argtypes = [_P, _D, C.POINTER(C.c_longlong)]
     lib.bse_spectrum.argtypes = [_P, C.c_int, C.c_int, _I, _D, _D, _D, C.c_double, C.c_double, C.c_int, _D, _D]
+    _F = C.POINTER(C.c_float)
+    lib.bse_mlp_param_count.argtypes = [C.c_int]
+    lib.bse_mlp_create.argtypes = [_P, C.c_int, C.c_int, _F, C.POINTER(_P)]
+    lib.bse_mlp_free.argtypes = [_P]
+    lib.bse_mlp_free.restype = None
+    lib.bse_mlp_get_params.argtypes = [_P, _P, _F]
+    lib.bse_mlp_forward.argtypes = [_P, _P, C.c_int, _P, _P]
+    lib.bse_mlp_gradients.argtypes = [_P, _P, C.c_int, _P, _P, _F, _D]
+    lib.bse_mlp_train_step.argtypes = [_P, _P, C.c_int, _P, _P, C.c_float, _D]
+    lib.bse_pairs_generate.argtypes = [_P, _P, C.c_int, _I, _I, _P, _P]
+    lib.bse_interp_set_learned.argtypes = [_P, _P, _P, C.c_int]
     _lib = lib
     return lib
 
@@ -145,6 +158,38 @@ class Interp:
         if self.handle:
             self.ctx.lib.bse_free_interp(self.handle)
             self.handle = None
+
+
+class Mlp:
+    def __init__(self, ctx: "Context", handle, d_in: int, nparams: int):
+        self.ctx, self.handle, self.d_in, self.nparams = ctx, handle, d_in, nparams
+
+    def params(self) -> np.ndarray:
+        p = np.zeros(self.nparams, dtype=np.float32)
+        self.ctx._check(self.ctx.lib.bse_mlp_get_params(self.ctx.h, self.handle, p.ctypes.data_as(C.POINTER(C.c_float))))
+        return p
+
+    def free(self):
+        if self.handle:
+            self.ctx.lib.bse_mlp_free(self.handle)
+            self.handle = None
+
+
+def mlp_unflatten(p: np.ndarray, d_in: int, width: int = 128):
+    """FP32 parameter vector (C-ABI layout) -> [[W, b], ...] float64 (oracle layout)."""
+    dims = [d_in, width, width, width, 2]
+    out, o = [], 0
+    for i in range(4):
+        w = p[o:o + dims[i + 1] * dims[i]].reshape(dims[i + 1], dims[i]).astype(np.float64)
+        o += dims[i + 1] * dims[i]
+        b = p[o:o + dims[i + 1]].astype(np.float64)
+        o += dims[i + 1]
+        out.append([w, b])
+    return out
+
+
+def mlp_flatten(params) -> np.ndarray:
+    return np.concatenate([np.concatenate([W.reshape(-1), b]) for W, b in params]).astype(np.float32)
 
 
 class Context:
@@ -219,6 +264,37 @@ class Context:
         cnt = (C.c_longlong * 5)()
         self._check(self.lib.bse_last_kernel_times(self.h, _dptr(ms), cnt))
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KERNEL_CLASSES)}
+
+    # -- learned near-diagonal residual
+    def bse_mlp_create(self, d_in: int, max_batch: int, init_params: np.ndarray) -> "Mlp":
+        p = np.ascontiguousarray(init_params, dtype=np.float32)
+        assert p.size == self.lib.bse_mlp_param_count(d_in)
+        h = _P()
+        self._check(self.lib.bse_mlp_create(self.h, d_in, max_batch, p.ctypes.data_as(C.POINTER(C.c_float)), C.byref(h)))
+        return Mlp(self, h, d_in, int(p.size))
+
+    def bse_mlp_forward(self, mlp: "Mlp", batch: int, X_ptr: int, out_ptr: int) -> None:
+        self._check(self.lib.bse_mlp_forward(self.h, mlp.handle, batch, _P(X_ptr), _P(out_ptr)))
+
+    def bse_mlp_gradients(self, mlp: "Mlp", batch: int, X_ptr: int, Y_ptr: int):
+        g = np.zeros(mlp.nparams, dtype=np.float32)
+        loss = C.c_double()
+        self._check(self.lib.bse_mlp_gradients(self.h, mlp.handle, batch, _P(X_ptr), _P(Y_ptr),
+                                               g.ctypes.data_as(C.POINTER(C.c_float)), C.byref(loss)))
+        return g, loss.value
+
+    def bse_mlp_train_step(self, mlp: "Mlp", batch: int, X_ptr: int, Y_ptr: int, lr: float) -> float:
+        loss = C.c_double()
+        self._check(self.lib.bse_mlp_train_step(self.h, mlp.handle, batch, _P(X_ptr), _P(Y_ptr), float(lr), C.byref(loss)))
+        return loss.value
+
+    def bse_pairs_generate(self, interp: Interp, kd: np.ndarray, kd2: np.ndarray, X_ptr: int, Y_ptr: int) -> None:
+        a = np.ascontiguousarray(kd, dtype=np.int32)
+        b = np.ascontiguousarray(kd2, dtype=np.int32)
+        self._check(self.lib.bse_pairs_generate(self.h, interp.handle, a.size, _iptr(a), _iptr(b), _P(X_ptr), _P(Y_ptr)))
+
+    def bse_interp_set_learned(self, interp: Interp, mlp: "Mlp | None", radius: int) -> None:
+        self._check(self.lib.bse_interp_set_learned(self.h, interp.handle, mlp.handle if mlp else None, radius))
 
     # -- bse_spectrum
     def bse_spectrum(self, a: np.ndarray, b: np.ndarray, pnorm2: np.ndarray, steps_done: np.ndarray,

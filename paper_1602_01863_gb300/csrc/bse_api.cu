@@ -38,7 +38,8 @@ void free_interp(bse_interp* s) {
     void* ptrs[] = {s->d_dE, s->d_Dv, s->d_Dc, s->d_P, s->d_list, s->d_list_start, s->d_hd, s->d_Hv, s->d_Hc,
                     s->d_hc, s->d_Q, s->d_R, s->d_X, s->d_U, s->d_Bop, s->d_part, s->d_vec[0],
                     s->d_vec[1], s->d_vec[2], s->d_part_dot, s->d_part_nrm, s->d_a, s->d_aim, s->d_b, s->d_stop,
-                    s->d_basis, s->d_cgs_part, s->d_cgs_h, s->d_pairs, s->d_clist, s->d_cstart};
+                    s->d_basis, s->d_cgs_part, s->d_cgs_h, s->d_pairs, s->d_clist, s->d_cstart,
+                    s->d_lker, s->d_lgrid, s->d_tw_fwd};
     for (void* p : ptrs) cudaFree(p);
     bse_tc_release(s);
     if (s->graph) cudaGraphExecDestroy(s->graph);

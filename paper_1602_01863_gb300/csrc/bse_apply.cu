@@ -1201,6 +1201,11 @@ int apply_h_typed(bse_ctx* ctx, bse_interp* s, int nchains, const void* psi_v, v
         Timer tm(ctx, prof, KC_PROLONG);
         launch_prolong<T>(ctx, s, nchains, s->d_R, m3 ? s->d_U : nullptr, psi, W, s->d_part_dot);
     }
+    if (s->learned) {
+        Timer tm(ctx, prof, KC_NEAR);
+        int rc = bse_apply_learned(ctx, s, nchains, psi, W, s->d_part_dot);
+        if (rc != BSE_OK) return rc;
+    }
     return BSE_OK;
 }
 

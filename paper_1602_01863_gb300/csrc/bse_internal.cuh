@@ -166,6 +166,12 @@ struct bse_interp {
     int basis_m = 0;
     double2* d_cgs_part = nullptr;   // [4][(m+1)][nblk]
     double2* d_cgs_h = nullptr;      // [4][m + 1]
+    // learned near-diagonal residual (M1 + periodic convolution with the stencil)
+    int learned = 0, learned_radius = 0;
+    float2* d_lker = nullptr;        // DFT of the stencil [t][t][L^3]
+    float2* d_lgrid = nullptr;       // 2 x [4][t][L^3] work grids
+    float2* d_tw_fwd = nullptr;      // [2 L] twiddles (forward, inverse)
+    float2* d_tw_inv = nullptr;
     // cached graph
     cudaGraphExec_t graph = nullptr;
     int graph_key[4] = {0, 0, 0, 0};
@@ -216,6 +222,7 @@ struct ApplyScratch {
     float* part;             // tile partials      (BF16 path only)
 };
 int bse_launch_near_field(bse_ctx* ctx, const bse_interp* s, int nchains, const void* X, void* U);
+int bse_apply_learned(bse_ctx* ctx, const bse_interp* s, int nchains, const void* psi, void* w, double2* dot);
 size_t bse_tc_part_bytes(const bse_interp* s);
 int bse_tc_apply_scratch(bse_ctx* ctx, const bse_interp* s, int nchains, __nv_bfloat16* bop, float* part, void* R);
 int bse_apply_scratch(bse_ctx* ctx, const bse_interp* s, int nvec, const void* x, void* y, const ApplyScratch& sc);

@@ -46,6 +46,10 @@ extern "C" int bse_apply_h_noalloc(bse_ctx* ctx, bse_interp* s, int nvec, const 
         ctx->err = "device index above the no-allocation table";
         return BSE_ERR_UNSUPPORTED;
     }
+    if (s->learned) {
+        ctx->err = "the learned correction is not available without allocation (use bse_apply_h)";
+        return BSE_ERR_UNSUPPORTED;
+    }
     if (cudaSetDevice(ctx->device) != cudaSuccess) return BSE_ERR_CUDA;
     void* base = nullptr;
     {

@@ -1,0 +1,201 @@
+"""Learned near-diagonal residual on the GPU against the FP64 oracle.
+
+The network's forward pass, gradients and Adam step are compared with
+oracle/learned.py using the same BF16-rounded weights (FP32 activations on
+the GPU: 1e-4-level agreement); pair data with the oracle's dense explicit
+and M1 matrices; the learned convolution with the oracle's stencil; and a
+network trained on the method's own pairs is checked to bring the spectrum of
+a held-out seed closer to the explicit one than M1 alone.
+"""
+import numpy as np
+import pytest
+
+from oracle import haydock as oh
+from oracle import interp as oi
+from oracle import learned as ol
+from oracle import model as om
+from paper_1602_01863_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1602_01863_gb300 import bse
+    torch.cuda.set_device(0)
+    c = bse.Context(0, torch.cuda.current_stream().cuda_stream)
+    yield c
+    c.close()
+
+
+def bf16_params(p, d_in):
+    """The GPU computes with BF16 weights and FP32 biases: round the weights."""
+    from paper_1602_01863_gb300 import bse
+    params = bse.mlp_unflatten(p, d_in)
+    for layer in params:
+        layer[0] = torch.from_numpy(layer[0]).to(torch.bfloat16).to(torch.float64).numpy()
+    return params
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def test_forward_gradients_and_adam_match_oracle(ctx):
+    from paper_1602_01863_gb300 import bse
+    d_in, B = 14, 96
+    p0 = bse.mlp_flatten(ol.init_params(d_in, seed=3))
+    mlp = ctx.bse_mlp_create(d_in, 256, p0)
+    rng = np.random.default_rng(8)
+    X = rng.standard_normal((B, d_in)).astype(np.float32)
+    Y = rng.standard_normal((B, 2)).astype(np.float32)
+    Xd, Yd = dev(X), dev(Y)
+    out = torch.empty((B, 2), dtype=torch.float32, device="cuda")
+    ctx.bse_mlp_forward(mlp, B, Xd.data_ptr(), out.data_ptr())
+    params = bf16_params(p0, d_in)
+    ref_out, cache = ol.forward(params, X.astype(np.float64))
+    assert np.abs(out.cpu().numpy() - ref_out).max() <= 1e-4 * np.abs(ref_out).max()
+    g, loss = ctx.bse_mlp_gradients(mlp, B, Xd.data_ptr(), Yd.data_ptr())
+    ref_loss, dout = ol.loss_and_grad_out(ref_out, Y.astype(np.float64))
+    ref_g = bse.mlp_flatten(ol.backward(params, cache, dout))
+    assert loss == pytest.approx(ref_loss, rel=1e-4)
+    assert np.abs(g - ref_g).max() <= 2e-4 * np.abs(ref_g).max()
+    # one Adam step: the FP32 master follows the oracle's update of the same gradients
+    ctx.bse_mlp_train_step(mlp, B, Xd.data_ptr(), Yd.data_ptr(), 1e-3)
+    p1 = mlp.params()
+    ref = bse.mlp_unflatten(p0, d_in)
+    grads = bse.mlp_unflatten(g, d_in)
+    m = [[np.zeros_like(W), np.zeros_like(b)] for W, b in ref]
+    v = [[np.zeros_like(W), np.zeros_like(b)] for W, b in ref]
+    ol.adam_update(ref, grads, m, v, step=1, lr=1e-3)
+    assert np.abs(p1 - bse.mlp_flatten(ref)).max() <= 1e-6
+    mlp.free()
+
+
+def test_pair_data_matches_oracle(ctx):
+    """Features and targets N_k (K_explicit - K_M1) for sampled near pairs of a
+    tiny system (coarse 2^3, n_div 4, 2v x 2c) against dense oracle matrices."""
+    m = synth.draw_model(17, 2, 2)
+    co = ctx.bse_build_coarse(m, 2, 0)
+    it = ctx.bse_interp_setup(co, 4, 0, 1.0, 0)
+    I = oi.Interp(m, 2, 4)
+    Hx, _ = om.explicit_dense_hamiltonian(m, 2, 4)
+    H1 = I.H_dense("m1")
+    rng = np.random.default_rng(9)
+    kd = rng.integers(0, I.Nk, 40)
+    kd2 = rng.integers(0, I.Nk, 40)
+    t = I.t
+    rows = 40 * t * t
+    X = torch.zeros((rows, 6 + 2 * t), dtype=torch.float32, device="cuda")
+    Y = torch.zeros((rows, 2), dtype=torch.float32, device="cuda")
+    ctx.bse_pairs_generate(it, kd, kd2, X.data_ptr(), Y.data_ptr())
+    tr1 = np.tile(np.repeat(np.arange(t), t), 40)
+    tr2 = np.tile(np.tile(np.arange(t), t), 40)
+    Xr, Yr = ol.residual_samples(I, Hx, H1, np.repeat(kd, t * t), np.repeat(kd2, t * t), tr1, tr2)
+    assert np.abs(X.cpu().numpy() - Xr).max() < 1e-6 * max(1.0, np.abs(Xr).max())
+    assert np.abs(Y.cpu().numpy() - Yr).max() <= 1e-4 * np.abs(Yr).max()
+    it.free()
+    co.free()
+
+
+def test_learned_convolution_matches_oracle_stencil(ctx):
+    from paper_1602_01863_gb300 import bse
+    m = synth.draw_model(18, 2, 2)
+    co = ctx.bse_build_coarse(m, 2, bse.PREC_F32)
+    it = ctx.bse_interp_setup(co, 4, bse.SCHEME_M1, 1.0, bse.PREC_F32)
+    I = oi.Interp(m, 2, 4)
+    d_in = 6 + 2 * I.t
+    p0 = bse.mlp_flatten(ol.init_params(d_in, seed=4))
+    mlp = ctx.bse_mlp_create(d_in, 4096, p0)
+    x = synth.random_vectors(5, (1, I.N)).astype(np.complex64)
+    xs = torch.from_numpy(x).cuda()
+    y0 = torch.empty_like(xs)
+    y1 = torch.empty_like(xs)
+    ctx.bse_apply_h(it, 1, xs.data_ptr(), y0.data_ptr())
+    ctx.bse_interp_set_learned(it, mlp, 3)
+    ctx.bse_apply_h(it, 1, xs.data_ptr(), y1.data_ptr())
+    got = (y1 - y0).cpu().numpy()[0].astype(np.complex128)
+    offs, T = ol.stencil(bf16_params(p0, d_in), I, 3, ol.mean_dE(I))
+    ref = ol.apply_stencil_direct(I, offs, T, x[0].astype(np.complex128))
+    assert np.abs(got - ref).max() <= 2e-3 * np.abs(ref).max()
+    ctx.bse_interp_set_learned(it, None, 3)
+    y2 = torch.empty_like(xs)
+    ctx.bse_apply_h(it, 1, xs.data_ptr(), y2.data_ptr())
+    assert torch.equal(y2, y0)                    # switching it off restores M1
+    mlp.free()
+    it.free()
+    co.free()
+
+
+@pytest.mark.slow
+def test_trained_network_improves_on_m1_for_held_out_seed(ctx):
+    """Coarse 4^3, 4v x 4c, n_div 4 (N = 65536), pairs closer than 2 coarse
+    spacings (8 dense steps).  Train on 8 seeds' pairs (~2M entries), apply on
+    held-out seed 299: Im eps of M1 + network is closer to the explicit oracle
+    than M1 alone."""
+    from paper_1602_01863_gb300 import bse
+    n, nd, radius = 4, 4, 8
+    d_in = 6 + 2 * 16
+    rng = np.random.default_rng(123)
+    Xs, Ys = [], []
+    L = n * nd
+    for seed in range(200, 208):
+        m = synth.draw_model(seed, 4, 4)
+        co = ctx.bse_build_coarse(m, n, bse.PREC_F32)
+        it = ctx.bse_interp_setup(co, nd, bse.SCHEME_M1, 1.0, bse.PREC_F32)
+        nblk = 1024
+        kd = rng.integers(0, it.Nk, nblk)
+        # partners within the radius: random offsets inside the ball
+        offs = ol.near_offsets(radius)
+        pick = offs[rng.integers(0, len(offs), nblk)]
+        g = om.dense_global(n, nd)
+        lin = {tuple(v): i for i, v in enumerate(g)}
+        kd2 = np.array([lin[tuple(np.mod(g[k] - d, L))] for k, d in zip(kd, pick)])
+        X = torch.zeros((nblk * 256, d_in), dtype=torch.float32, device="cuda")
+        Y = torch.zeros((nblk * 256, 2), dtype=torch.float32, device="cuda")
+        ctx.bse_pairs_generate(it, kd, kd2, X.data_ptr(), Y.data_ptr())
+        Xs.append(X)
+        Ys.append(Y)
+        it.free()
+        co.free()
+    X = torch.cat(Xs)
+    Y = torch.cat(Ys)
+    mlp = ctx.bse_mlp_create(d_in, 4096, bse.mlp_flatten(ol.init_params(d_in, seed=11)))
+    perm_rng = np.random.default_rng(5)
+    nsamp = X.shape[0]
+    first = last = None
+    for step in range(2500):
+        idx = torch.from_numpy(perm_rng.integers(0, nsamp, 4096)).cuda()
+        xb = X[idx].contiguous()
+        yb = Y[idx].contiguous()
+        lr = 2e-3 if step < 1500 else 5e-4
+        loss = ctx.bse_mlp_train_step(mlp, 4096, xb.data_ptr(), yb.data_ptr(), lr)
+        first = loss if first is None else first
+        last = loss
+    assert last < 0.5 * first
+    # held-out seed: M1, M1 + network, M3 against the explicit oracle
+    m = synth.draw_model(299, 4, 4)
+    w = synth.frequency_grid(1000)
+    e = np.array([[1.0, 0.0, 0.0]])
+    ex = om.ExplicitOperator(m, n, nd)
+    P = om.polarised_dipole(ex.gm, e[0])
+    ra, rb, rpn2, _ = oh.haydock(ex.apply, P, 200, "none")
+    ref = oh.epsilon(ra, rb, rpn2, 1.0 / (L ** 3), 0.1, w)
+    errs = {}
+    for name, scheme, learned in (("m1", bse.SCHEME_M1, False), ("m1+mlp", bse.SCHEME_M1, True), ("m3", bse.SCHEME_M3, False)):
+        co = ctx.bse_build_coarse(m, n, bse.PREC_F32)
+        it = ctx.bse_interp_setup(co, nd, scheme, 1.0, bse.PREC_F32)
+        if learned:
+            ctx.bse_interp_set_learned(it, mlp, radius)
+        a, b, pn2, st, _ = ctx.bse_haydock_run([it], [1], e, 200, 0)
+        eps = ctx.bse_spectrum(a, b, pn2, st, 1.0 / (L ** 3), 0.1, w)
+        errs[name] = oh.spectrum_error(eps[0].imag, ref.imag)
+        it.free()
+        co.free()
+    print("Im eps error vs explicit:", errs)
+    assert errs["m1+mlp"] < errs["m1"]
+    mlp.free()
