@@ -251,7 +251,7 @@ int bse_mlp_train_step(bse_ctx* ctx, bse_mlp* mlp, int batch, const float* X, co
                        double* loss);
 /* Training data from the method: for nblocks sampled dense pairs
  * (host_kd[i], host_kd2[i]) of `interp` (complex128 or complex64 K_c,
- * t <= 16), all t x t entries: features X [nblocks t^2][6 + 2t] and targets
+ * t <= 24), all t x t entries: features X [nblocks t^2][6 + 2t] and targets
  * Y = N_k (K_explicit - K_M1) [nblocks t^2][2] (device), row order
  * (pair, vc, v'c').  K_explicit is the model kernel on the dense mesh in FP64
  * (Eqs. bse2-bse3b with the model); K_M1 = (1/N_div) F K_c F^H (Eq. interp1). */

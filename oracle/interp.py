@@ -34,7 +34,7 @@ class Interp:
         self.t = model.nv * model.nc
         self.width = width
         self.coarse = om.GridModel(model, om.coarse_coords(n), n)
-        self.dense = om.GridModel(model, om.dense_global(n, nd), n * nd)
+        self.dense = om.GridModel(model, om.dense_global(n, nd), n * nd, with_form_factors=False)
         if dense_gauge_twist is not None:
             # Gauge change of the dense states, U(k) -> U(k) Phi(k) (a phase per
             # band for non-degenerate bands).  P follows from the rotated
@@ -126,6 +126,27 @@ class Interp:
         """H^{M1} psi = Delta E psi + (1/N_div) F K_c (F^H psi) (Eqs. matmul1-3)."""
         Kc = self.Kc if Kc is None else Kc
         return self.dE * psi + self.prolong(Kc @ self.restrict(psi)) / self.Ndiv
+
+    def apply_m1_rows(self, psi: np.ndarray, rows: np.ndarray) -> np.ndarray:
+        """(H^{M1} psi) at the dense points `rows` (Eqs. matmul1-3) with only the
+        K_c rows of their corners computed (for meshes whose K_c is too large
+        to store): [len(rows), t]."""
+        Q = self.restrict(psi)
+        corners = np.unique(self.corner[rows][self.f[rows] != 0])
+        Kr = om.kernel_rows(self.coarse, corners)
+        Rc = (Kr @ Q).reshape(len(corners), self.nv, self.nc)
+        pos = {int(c): i for i, c in enumerate(corners)}
+        t = self.t
+        out = np.zeros((len(rows), t), dtype=np.complex128)
+        for r, kd in enumerate(rows):
+            s = np.zeros((self.nv, self.nc), dtype=np.complex128)
+            for l in range(8):
+                if self.f[kd, l] == 0.0:
+                    continue
+                R = Rc[pos[int(self.corner[kd, l])]]
+                s += self.f[kd, l] * (self.Dv[kd, l].T @ R @ self.Dc[kd, l].conj())
+            out[r] = self.dE[kd * t:(kd + 1) * t] * psi[kd * t:(kd + 1) * t] + s.reshape(-1) / self.Ndiv
+        return out
 
     def near_field_rows(self, psi: np.ndarray, rows: np.ndarray) -> np.ndarray:
         """(K^{M3} - K^{M1}) psi at the dense points `rows`, pair by pair.

@@ -184,7 +184,7 @@ def coulomb_bar() -> np.ndarray:
 class GridModel:
     """The model evaluated on one periodic L^3 grid of points (integer coords)."""
 
-    def __init__(self, model: ModelParams, gint: np.ndarray, L: int):
+    def __init__(self, model: ModelParams, gint: np.ndarray, L: int, with_form_factors: bool = True):
         self.model = model
         self.gint = gint
         self.L = L
@@ -192,7 +192,7 @@ class GridModel:
         self.Uv = gauge(model.gen_v, self.kfrac)
         self.Uc = gauge(model.gen_c, self.kfrac)
         self.dE = energies(model, self.kfrac)
-        self.M = form_factors(model, self.Uv, self.Uc, self.kfrac)
+        self.M = form_factors(model, self.Uv, self.Uc, self.kfrac) if with_form_factors else None
         self.P = dipoles(model, self.Uv, self.Uc, self.kfrac)
 
 
@@ -233,6 +233,29 @@ def kernel_matrix(gm: GridModel) -> np.ndarray:
     D = np.einsum("abvw,abcd,ab->avcbwd", Ov, Oc, H).reshape(npts * t, npts * t)
     K -= (pref / m.eps_inf) * D
     return K
+
+
+def kernel_rows(gm: GridModel, pts: np.ndarray) -> np.ndarray:
+    """Rows of the same kernel (kernel_matrix) for the grid points `pts`
+    only: [len(pts) * t, N], computed pair by pair from the model, for grids
+    whose full matrix is too large to store."""
+    m = gm.model
+    npts = gm.gint.shape[0]
+    t = m.nv * m.nc
+    pref = m.e_k / npts
+    out = np.zeros((len(pts), t, npts, t), dtype=np.complex128)
+    if m.exchange_on:
+        Mflat = gm.M.transpose(0, 2, 3, 1)                                   # [p, v, c, G]
+        rowsM = Mflat[pts].reshape(len(pts), t, 26)
+        allM = Mflat.reshape(npts, t, 26)
+        out += 2 * pref * np.einsum("avg,g,bwg->avbw", rowsM.conj(), coulomb_bar(), allM)
+    Ov = overlap_v(gm.Uv[pts][:, None], gm.Uv[None, :])                    # [a, b, v, v']
+    Oc = overlap_c(gm.Uc[pts][:, None], gm.Uc[None, :])
+    ht = h_table(gm.L, lambda d: h_full(d, gm.L, m))
+    dg = np.mod(gm.gint[pts][:, None, :] - gm.gint[None, :, :], gm.L)
+    H = ht[dg[..., 0], dg[..., 1], dg[..., 2]]
+    out -= (pref / m.eps_inf) * np.einsum("abvw,abcd,ab->avcbwd", Ov, Oc, H).reshape(len(pts), t, npts, t)
+    return out.reshape(len(pts) * t, npts * t)
 
 
 def head_matrix(gm: GridModel) -> tuple[np.ndarray, np.ndarray]:

@@ -281,7 +281,7 @@ __device__ void dmat_expm_i(const double2* A, int n, double2* E) {
 // model kernel (FP64, dense weight e_k / N_k) and of K^{M1} = (1/N_div) F K_c F^H
 // (FP32 from the handle's tables), written as network features and targets.
 template <typename T>
-__global__ void __launch_bounds__(256) k_pairs(
+__global__ void __launch_bounds__(576) k_pairs(
     const int* __restrict__ kd1, const int* __restrict__ kd2, int nblocks, const double2* __restrict__ gen_v,
     const double2* __restrict__ gen_c, const double2* __restrict__ mu, const typename Cx<T>::V* __restrict__ Kc,
     const typename Cx<T>::V* __restrict__ Dv, const typename Cx<T>::V* __restrict__ Dc, const T* __restrict__ dE,
@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(256) k_pairs(
     const int blk = blockIdx.x;
     if (blk >= nblocks) return;
     const int t = nv * nc, Ndiv = nd * nd * nd, L = n * nd, nk = n * n * n * Ndiv, Nc = t * n * n * n;
-    constexpr int PT = 16;                     // t <= 16 (checked by the host)
+    constexpr int PT = 24;                     // t <= 24 (checked by the host)
     __shared__ double2 Uv[2][BSE_MAX_BANDS * BSE_MAX_BANDS], Uc[2][BSE_MAX_BANDS * BSE_MAX_BANDS];
     __shared__ double2 M[2][26][PT];
     __shared__ float2 Fa[PT * PT], Fb[PT * PT], Tm[PT * PT];
@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(256) k_pairs(
     }
     // K^{M1} block, accumulated in Tm via the factored form
     float2 kacc = make_float2(0.f, 0.f);
-    const int e1 = threadIdx.x / t, e2 = threadIdx.x % t;        // (vc, v'c') of this thread (t*t <= 256 assumed)
+    const int e1 = threadIdx.x / t, e2 = threadIdx.x % t;        // (vc, v'c') of this thread (blockDim >= t*t)
     const bool mine = threadIdx.x < t * t;
     const int cell0 = kk[0] / Ndiv, js0 = kk[0] % Ndiv, cell1 = kk[1] / Ndiv, js1 = kk[1] % Ndiv;
     const Int3 c0 = unflat3(cell0, n), c1 = unflat3(cell1, n);
@@ -720,7 +720,8 @@ int bse_pairs_generate(bse_ctx* ctx, const bse_interp* s, int nblocks, const int
     if (!ctx || !s || !host_kd || !host_kd2 || !X || !Y || nblocks < 1) return BSE_ERR_ARG;
     const bse_coarse* c = s->co;
     if (c->kc_prec == BSE_PREC_BF16) { ctx->err = "pair data needs a complex128 or complex64 K_c"; return BSE_ERR_UNSUPPORTED; }
-    if (s->t * s->t > 256) { ctx->err = "pair data supports t <= 16"; return BSE_ERR_UNSUPPORTED; }
+    if (s->t > 24) { ctx->err = "pair data supports t <= 24"; return BSE_ERR_UNSUPPORTED; }
+    const int pthreads = std::max(64, (s->t * s->t + 31) / 32 * 32);
     for (int i = 0; i < nblocks; ++i)
         if (host_kd[i] < 0 || host_kd[i] >= s->nk || host_kd2[i] < 0 || host_kd2[i] >= s->nk) {
             ctx->err = "dense index out of range";
@@ -735,12 +736,12 @@ int bse_pairs_generate(bse_ctx* ctx, const bse_interp* s, int nblocks, const int
     cudaMemcpy(d2, host_kd2, sizeof(int) * nblocks, cudaMemcpyHostToDevice);
     const int d_in = 6 + 2 * s->t;
     if (s->vec_prec == BSE_PREC_F64)
-        k_pairs<double><<<nblocks, 256, 0, ctx->stream>>>(d1, d2, nblocks, c->d_gen_v, c->d_gen_c, c->d_mu, (const double2*)c->d_kc,
+        k_pairs<double><<<nblocks, pthreads, 0, ctx->stream>>>(d1, d2, nblocks, c->d_gen_v, c->d_gen_c, c->d_mu, (const double2*)c->d_kc,
                                                          (const double2*)s->d_Dv, (const double2*)s->d_Dc, (const double*)s->d_dE,
                                                          s->n, s->nd, s->nv, s->nc, s->nb1, c->e_k, 1.0 / c->eps_inf, c->kappa,
                                                          c->direct_shells, c->exchange_on, d_in, X, Y);
     else
-        k_pairs<float><<<nblocks, 256, 0, ctx->stream>>>(d1, d2, nblocks, c->d_gen_v, c->d_gen_c, c->d_mu, (const float2*)c->d_kc,
+        k_pairs<float><<<nblocks, pthreads, 0, ctx->stream>>>(d1, d2, nblocks, c->d_gen_v, c->d_gen_c, c->d_mu, (const float2*)c->d_kc,
                                                         (const float2*)s->d_Dv, (const float2*)s->d_Dc, (const float*)s->d_dE,
                                                         s->n, s->nd, s->nv, s->nc, s->nb1, c->e_k, 1.0 / c->eps_inf, c->kappa,
                                                         c->direct_shells, c->exchange_on, d_in, X, Y);

@@ -1,0 +1,88 @@
+"""Full-size parity on sampled outputs.
+
+At the benchmark's sizes the oracle cannot form H, so one application
+y = H x of the GPU path is compared with the oracle at a few sampled dense
+points (K_c rows of their corners built on demand, the M3 near field pair by
+pair).  Tolerances: FP64 plain path 1e-11 relative to max |y - dE x|; BF16
+K_c paths 5e-3 (BF16 rounding of K_c, FP32 vectors).
+"""
+import numpy as np
+import pytest
+
+from oracle import interp as oi
+from oracle import learned as ol
+from paper_1602_01863_gb300 import synth
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1602_01863_gb300 import bse
+    torch.cuda.set_device(0)
+    c = bse.Context(0, torch.cuda.current_stream().cuda_stream)
+    yield c
+    c.close()
+
+
+def _apply(ctx, it, x):
+    dt = torch.complex128 if it.vec_prec == 0 else torch.complex64
+    xs = torch.from_numpy(np.ascontiguousarray(x)).to(dt).cuda()
+    ys = torch.empty_like(xs)
+    ctx.bse_apply_h(it, x.shape[0], xs.data_ptr(), ys.data_ptr())
+    torch.cuda.synchronize()
+    return ys.cpu().numpy().astype(np.complex128)
+
+
+def _check_rows(I, x, y, rows, m3, tol):
+    ref = I.apply_m1_rows(x, rows)
+    if m3:
+        ref = ref + I.near_field_rows(x, rows)
+    got = y.reshape(I.Nk, I.t)[rows]
+    dex = (I.dE * x).reshape(I.Nk, I.t)[rows]
+    assert np.abs(got - ref).max() <= tol * np.abs(ref - dex).max()
+
+
+@pytest.mark.parametrize("kc_prec,vec_prec,tol", [(2, 1, 5e-3), (0, 0, 1e-11)])
+def test_single_system_size_m3(ctx, kc_prec, vec_prec, tol):
+    """Coarse 8^3, 4v x 4c, n_div 4 (N = 524288), Method 3, w = 1."""
+    s = synth.single_system()
+    co = ctx.bse_build_coarse(s.model, s.n_coarse, kc_prec)
+    it = ctx.bse_interp_setup(co, s.n_div, 1, 1.0, vec_prec)
+    x = synth.random_vectors(31, (1, it.N))
+    y = _apply(ctx, it, x)[0]
+    I = oi.Interp(s.model, s.n_coarse, s.n_div, width=1.0, build_dense_kc=False)
+    rows = np.array([0, 4097, 17000, it.Nk - 1])
+    _check_rows(I, x[0], y, rows, True, tol)
+    it.free()
+    co.free()
+
+
+def test_largest_size_m1_and_learned_run(ctx):
+    """Coarse 12^3, 4v x 6c, n_div 4 (N = 2654208, BF16 K_c of 41472^2 = 6.9 GB):
+    sampled rows of one M1 application against the oracle; then 3 chains with
+    the learned correction (radius 8 dense steps, t = 24 stencil on the 48^3
+    mesh) for 12 steps: finite, positive b, Im eps >= 0."""
+    from paper_1602_01863_gb300 import bse
+    s = synth.largest_system()
+    co = ctx.bse_build_coarse(s.model, s.n_coarse, bse.PREC_BF16)
+    it = ctx.bse_interp_setup(co, s.n_div, bse.SCHEME_M1, 1.0, bse.PREC_F32)
+    x = synth.random_vectors(32, (1, it.N))
+    y = _apply(ctx, it, x)[0]
+    I = oi.Interp(s.model, s.n_coarse, s.n_div, build_dense_kc=False)
+    rows = np.array([3, 50000, it.Nk - 5])
+    _check_rows(I, x[0], y, rows, False, 5e-3)
+    d_in = 6 + 2 * it.t
+    mlp = ctx.bse_mlp_create(d_in, 4096, bse.mlp_flatten(ol.init_params(d_in, seed=7)))
+    ctx.bse_interp_set_learned(it, mlp, 8)
+    a, b, pn2, st, rc = ctx.bse_haydock_run([it], [3], s.pol_dirs, 12, bse.USE_GRAPH)
+    assert np.all(np.isfinite(a)) and np.all(b[:, 1:] > 0)
+    eps = ctx.bse_spectrum(a, b, pn2, st, 1.0 / it.Nk, 0.1, synth.frequency_grid(2000))
+    assert np.all(eps.imag > -1e-9 * np.abs(eps.imag).max())
+    mlp.free()
+    it.free()
+    co.free()

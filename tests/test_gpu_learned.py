@@ -132,13 +132,14 @@ def test_learned_convolution_matches_oracle_stencil(ctx):
 
 
 @pytest.mark.slow
-def test_trained_network_improves_on_m1_for_held_out_seed(ctx):
-    """Coarse 4^3, 4v x 4c, n_div 4 (N = 65536), pairs closer than 2 coarse
-    spacings (8 dense steps).  Train on 8 seeds' pairs (~2M entries), apply on
-    held-out seed 299: Im eps of M1 + network is closer to the explicit oracle
-    than M1 alone."""
+@pytest.mark.parametrize("n,steps", [(4, 200), (8, 300)])
+def test_trained_network_improves_on_m1_for_held_out_seed(ctx, n, steps):
+    """4v x 4c, n_div 4, coarse 4^3 (N = 65536) and the specified coarse 8^3
+    (N = 524288); pairs closer than 2 coarse spacings (8 dense steps).  Train
+    on 8 seeds' pairs (~2M entries), apply on held-out seed 299: Im eps of
+    M1 + network is closer to the explicit oracle than M1 alone."""
     from paper_1602_01863_gb300 import bse
-    n, nd, radius = 4, 4, 8
+    nd, radius = 4, 8
     d_in = 6 + 2 * 16
     rng = np.random.default_rng(123)
     Xs, Ys = [], []
@@ -183,7 +184,7 @@ def test_trained_network_improves_on_m1_for_held_out_seed(ctx):
     e = np.array([[1.0, 0.0, 0.0]])
     ex = om.ExplicitOperator(m, n, nd)
     P = om.polarised_dipole(ex.gm, e[0])
-    ra, rb, rpn2, _ = oh.haydock(ex.apply, P, 200, "none")
+    ra, rb, rpn2, _ = oh.haydock(ex.apply, P, steps, "none")
     ref = oh.epsilon(ra, rb, rpn2, 1.0 / (L ** 3), 0.1, w)
     errs = {}
     for name, scheme, learned in (("m1", bse.SCHEME_M1, False), ("m1+mlp", bse.SCHEME_M1, True), ("m3", bse.SCHEME_M3, False)):
@@ -191,11 +192,11 @@ def test_trained_network_improves_on_m1_for_held_out_seed(ctx):
         it = ctx.bse_interp_setup(co, nd, scheme, 1.0, bse.PREC_F32)
         if learned:
             ctx.bse_interp_set_learned(it, mlp, radius)
-        a, b, pn2, st, _ = ctx.bse_haydock_run([it], [1], e, 200, 0)
+        a, b, pn2, st, _ = ctx.bse_haydock_run([it], [1], e, steps, 0)
         eps = ctx.bse_spectrum(a, b, pn2, st, 1.0 / (L ** 3), 0.1, w)
         errs[name] = oh.spectrum_error(eps[0].imag, ref.imag)
         it.free()
         co.free()
-    print("Im eps error vs explicit:", errs)
+    print(f"coarse {n}^3: Im eps error vs explicit:", errs)
     assert errs["m1+mlp"] < errs["m1"]
     mlp.free()

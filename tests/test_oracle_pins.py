@@ -339,3 +339,14 @@ def test_sum_rules():
     assert np.sum(wts) == pytest.approx(pn2, rel=1e-12)
     assert np.sum(wts * E) == pytest.approx(np.vdot(P, H @ P).real, rel=1e-12)
     assert np.sum(wts * E) == pytest.approx(pn2 * a[0], rel=1e-12)
+
+
+def test_sampled_rows_match_matrix_free_apply():
+    """apply_m1_rows (K_c rows built on demand) equals the full matrix-free M1."""
+    I = tiny_interp(n=3, nd=2, nv=2, nc=3)
+    v = synth.random_vectors(12, I.N)
+    rows = np.array([0, 7, 100, I.Nk - 1])
+    full = I.apply_m1(v).reshape(I.Nk, I.t)[rows]
+    assert np.abs(I.apply_m1_rows(v, rows) - full).max() < 1e-13
+    Kr = om.kernel_rows(I.coarse, np.array([1, 5]))
+    assert np.abs(Kr - I.Kc[np.r_[I.t:2 * I.t, 5 * I.t:6 * I.t]]).max() < 1e-15
