@@ -57,6 +57,10 @@ extern "C" {
 #define BSE_SCHEME_M3   1  /* Method 3: M1 plus divergence treatment on near pairs  */
 #define BSE_NB1        16  /* OR-flag: one-neighbour weights (Eq. eqRL, f = 1 on
                               the nearest coarse corner) instead of trilinear 8NB   */
+#define BSE_NF_CUDA_CORES 32 /* OR-flag: apply the M3 near field on the CUDA cores
+                              even where the tensor-core kernel applies (FP32
+                              vectors, t <= 16, n_div <= 4); same result to
+                              TF32 rounding of the head blocks and y1, z        */
 
 /* ------------------------------------------------------------ Haydock flags */
 #define BSE_REORTH_CGS2   1  /* full reorthogonalisation, classical Gram-Schmidt x2 */

@@ -26,7 +26,7 @@ BSE_ERR_UNSUPPORTED = -5
 BSE_WARN_BREAKDOWN = 1
 
 PREC_F64, PREC_F32, PREC_BF16 = 0, 1, 2
-SCHEME_M1, SCHEME_M3, NB1 = 0, 1, 16
+SCHEME_M1, SCHEME_M3, NB1, NF_CUDA_CORES = 0, 1, 16, 32
 REORTH_CGS2, USE_GRAPH, PROFILE = 1, 2, 4
 
 KERNEL_CLASSES = ("restrict", "kc_apply", "prolong", "near_field", "lanczos")

@@ -39,7 +39,8 @@ void free_interp(bse_interp* s) {
                     s->d_hc, s->d_Q, s->d_R, s->d_X, s->d_U, s->d_Bop, s->d_part, s->d_vec[0],
                     s->d_vec[1], s->d_vec[2], s->d_part_dot, s->d_part_nrm, s->d_a, s->d_aim, s->d_b, s->d_stop,
                     s->d_basis, s->d_cgs_part, s->d_cgs_h, s->d_pairs, s->d_clist, s->d_cstart,
-                    s->d_lker, s->d_lgrid, s->d_tw_fwd};
+                    s->d_lker, s->d_lgrid, s->d_tw_fwd, s->d_tc_rows, s->d_tc_urow,
+                    s->d_tc_rec, s->d_tc_urec, s->d_tc_uinfo};
     for (void* p : ptrs) cudaFree(p);
     bse_tc_release(s);
     if (s->graph) cudaGraphExecDestroy(s->graph);
@@ -171,7 +172,7 @@ int bse_interp_setup(bse_ctx* ctx, const bse_coarse* c, int n_div, int scheme, d
     *out = nullptr;
     if (!c) return set_arg_error(ctx, "coarse handle is NULL");
     if (n_div < 1 || n_div > 16) return set_arg_error(ctx, "n_div must be in 1..16");
-    const int base = scheme & ~BSE_NB1;
+    const int base = scheme & ~(BSE_NB1 | BSE_NF_CUDA_CORES);
     if (base != BSE_SCHEME_M1 && base != BSE_SCHEME_M3) return set_arg_error(ctx, "unknown scheme");
     if (vec_prec != BSE_PREC_F64 && vec_prec != BSE_PREC_F32) return set_arg_error(ctx, "vec_prec must be F64 or F32");
     if ((c->kc_prec == BSE_PREC_F64) != (vec_prec == BSE_PREC_F64)) {
@@ -191,6 +192,7 @@ int bse_interp_setup(bse_ctx* ctx, const bse_coarse* c, int n_div, int scheme, d
     s->co = c; s->n = c->n; s->nd = n_div; s->Ndiv = n_div * n_div * n_div; s->nk = (int)nk;
     s->nv = c->nv; s->nc = c->nc; s->t = c->t; s->N = (int)(nk * c->t);
     s->scheme = base; s->nb1 = (scheme & BSE_NB1) ? 1 : 0; s->vec_prec = vec_prec; s->width = width_w;
+    s->nf_force_cuda_cores = (scheme & BSE_NF_CUDA_CORES) ? 1 : 0;
     int rc = bse_setup_interp_device(ctx, s);
     if (rc != BSE_OK) { free_interp(s); return rc; }
     *out = s;

@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(256) k_restrict(
     for (int q = 0; q < 2; ++q) { const int e = lane + 32 * q; n3q[q] = e / nc; n4q[q] = e % nc; }
     for (int p = warp; p < 8 * Ndiv; p += kRestrictWarps) {
         const int l = p / Ndiv, js = p % Ndiv;
-        const T f = (T)interp_weight(js, l, nd, nb1);
+        const T f = interp_weight_as<T>(js, l, nd, nb1);
         if (f == (T)0) continue;                                   // warp-uniform
         const int src = flat3(i.a - ((l >> 2) & 1), i.b - ((l >> 1) & 1), i.c - (l & 1), n);
         const size_t kd = (size_t)src * Ndiv + js;
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(256) k_restrict_rb(
             for (int b = 0; b < NC; ++b) acc[a][b] = make_float2(0.f, 0.f);
         for (int cand = tid; cand < 8 * Ndiv; cand += 256) {
             const int l = cand / Ndiv, js = cand - l * Ndiv;
-            const float f = (float)interp_weight(js, l, nd, nb1);
+            const float f = interp_weight_f(js, l, nd, nb1);
             if (f == 0.f) continue;
             const int src = flat3(i.a - ((l >> 2) & 1), i.b - ((l >> 1) & 1), i.c - (l & 1), n);
             const size_t kd = (size_t)src * Ndiv + js;
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(BSE_VEC_THREADS) k_prolong_rb(
 #pragma unroll
             for (int b = 0; b < NC; ++b) s[a][b] = make_float2(0.f, 0.f);
         for (int l = 0; l < 8; ++l) {
-            const float f = (float)interp_weight(js, l, nd, nb1);
+            const float f = interp_weight_f(js, l, nd, nb1);
             if (f == 0.f) continue;
             const int cc = flat3(ci.a + ((l >> 2) & 1), ci.b + ((l >> 1) & 1), ci.c + (l & 1), n);
             const float2* dv = Dv + ((size_t)kd * 8 + l) * NV * NV;
@@ -411,7 +411,7 @@ __global__ void __launch_bounds__(256) k_near_field(
         __syncthreads();
         for (int idx = threadIdx.x; idx < 8 * t; idx += blockDim.x) {
             const int l = idx / t, e = idx % t;
-            if (interp_weight(js, l, nd, nb1) == 0.0) continue;
+            if (!interp_active(js, l, nd, nb1)) continue;
             const int l1 = (l >> 2) & 1, l2 = (l >> 1) & 1, l3 = l & 1;
             const int kt = flat3(ci.a + l1, ci.b + l2, ci.c + l3, n);
             const int n1 = e / nc, n2 = e % nc;
@@ -776,7 +776,7 @@ __global__ void __launch_bounds__(BSE_VEC_THREADS) k_prolong(
 #pragma unroll
         for (int ch = 0; ch < BSE_MAX_CHAINS; ++ch) { acc[ch][0] = czero<V>(); acc[ch][1] = czero<V>(); }
         for (int l = 0; l < 8; ++l) {
-            const T f = (T)interp_weight(js, l, nd, nb1);
+            const T f = interp_weight_as<T>(js, l, nd, nb1);
             if (f == (T)0) continue;                               // warp-uniform
             const int cc = flat3(ci.a + ((l >> 2) & 1), ci.b + ((l >> 1) & 1), ci.c + (l & 1), n);
             const V* dv = Dv + ((size_t)kd * 8 + l) * nv * nv;
@@ -1607,6 +1607,7 @@ template <typename T>
 int launch_near_typed(bse_ctx* ctx, const bse_interp* s, int nchains, const void* X, void* U) {
     using V = typename Cx<T>::V;
     if constexpr (std::is_same<T, float>::value) {
+        if (s->nf_tc && !s->nf_force_cuda_cores) return bse_near_tc_launch(ctx, s, nchains, X, U);
         if (s->cell_smem && s->npairs <= 512) {
             // rows of the slot staging each of the 512 threads owns
             const int rows = (s->npairs + 512 / s->t - 1) / (512 / s->t);

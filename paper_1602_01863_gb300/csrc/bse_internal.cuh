@@ -78,16 +78,30 @@ __host__ __device__ inline int flat3(int a, int b, int c, int n) {
 // (l = l1*4 + l2*2 + l3): trilinear f^l_j = (1 - j/n_div | j/n_div) per axis
 // (Sec. 3, Eq. interpwfn), or the one-neighbour scheme (Eq. eqRL: f = 1 on
 // the nearest corner, j/n_div = 1/2 going to l = 0).
-__host__ __device__ inline double interp_weight(int js, int l, int nd, int nb1) {
+// Trilinear weight f^l_j = prod_a (l_a ? j_a / n_div : 1 - j_a / n_div) as an
+// integer numerator over n_div^3 (exact for n_div <= 16); one-neighbour
+// weights (nb1) are 0 or 1 with denominator 1.
+__host__ __device__ inline int interp_num(int js, int l, int nd, int nb1) {
     const int j1 = js / (nd * nd), j2 = (js / nd) % nd, j3 = js % nd;
     const int l1 = (l >> 2) & 1, l2 = (l >> 1) & 1, l3 = l & 1;
-    if (nb1) {
-        return ((2 * j1 > nd) == l1 && (2 * j2 > nd) == l2 && (2 * j3 > nd) == l3) ? 1.0 : 0.0;
-    }
-    const double f1 = l1 ? (double)j1 / nd : 1.0 - (double)j1 / nd;
-    const double f2 = l2 ? (double)j2 / nd : 1.0 - (double)j2 / nd;
-    const double f3 = l3 ? (double)j3 / nd : 1.0 - (double)j3 / nd;
-    return f1 * f2 * f3;
+    if (nb1) return ((2 * j1 > nd) == l1 && (2 * j2 > nd) == l2 && (2 * j3 > nd) == l3) ? 1 : 0;
+    return (l1 ? j1 : nd - j1) * (l2 ? j2 : nd - j2) * (l3 ? j3 : nd - j3);
+}
+// whether f^l_j != 0 (integer test, no division)
+__host__ __device__ inline bool interp_active(int js, int l, int nd, int nb1) { return interp_num(js, l, nd, nb1) != 0; }
+__host__ __device__ inline double interp_weight(int js, int l, int nd, int nb1) {
+    const int num = interp_num(js, l, nd, nb1);
+    return nb1 ? (double)num : (double)num / (double)(nd * nd * nd);
+}
+// the same weight in FP32 (one correctly rounded division)
+__host__ __device__ inline float interp_weight_f(int js, int l, int nd, int nb1) {
+    const int num = interp_num(js, l, nd, nb1);
+    return nb1 ? (float)num : (float)num / (float)(nd * nd * nd);
+}
+template <typename T>
+__host__ __device__ inline T interp_weight_as(int js, int l, int nd, int nb1) {
+    if constexpr (sizeof(T) == sizeof(float)) return interp_weight_f(js, l, nd, nb1);
+    else return interp_weight(js, l, nd, nb1);
 }
 
 // ------------------------------------------------------------------ handles
@@ -140,6 +154,17 @@ struct bse_interp {
     int* d_clist = nullptr;
     int* d_cstart = nullptr;         // [Ndiv][nslot + 1]
     size_t cell_smem = 0;            // dynamic shared memory of the cell kernel (0: not usable)
+    int nf_tc = 0;                   // the tensor-core near field serves this handle
+    size_t nf_tc_smem = 0;
+    int nf_tc_units = 0;             // units (slot pieces) of the near pattern
+    int nf_tc_rec_max = 0;           // largest unit record (ints)
+    int nf_tc_npart = 0;             // most partial sums any unit needs
+    int* d_tc_rows = nullptr;        // staged source rows of every unit: js | corner << 16
+    int2* d_tc_urow = nullptr;       // per unit {first row, rows}
+    int* d_tc_rec = nullptr;         // unit records: schedule and contribution list
+    int2* d_tc_urec = nullptr;       // per unit {record offset, record length} (ints)
+    int2* d_tc_uinfo = nullptr;      // per unit {slot, slot ordinal | first << 16 | last << 17}
+    int nf_force_cuda_cores = 0;     // BSE_NF_CUDA_CORES: keep the CUDA-core near-field kernels
     void* d_hd = nullptr;            // T [n_near]   h_head at dense near offsets
     void* d_Hv = nullptr;            // V [nkc][nrel][nv*nv]
     void* d_Hc = nullptr;            // V [nkc][nrel][nc*nc]
@@ -223,6 +248,9 @@ struct ApplyScratch {
 };
 int bse_launch_near_field(bse_ctx* ctx, const bse_interp* s, int nchains, const void* X, void* U);
 int bse_apply_learned(bse_ctx* ctx, const bse_interp* s, int nchains, const void* psi, void* w, double2* dot);
+int bse_near_tc_prepare(bse_ctx* ctx, bse_interp* s, const std::vector<int>& pairs, const std::vector<int>& clist,
+                        const std::vector<int>& cstart);
+int bse_near_tc_launch(bse_ctx* ctx, const bse_interp* s, int nchains, const void* X, void* U);
 size_t bse_tc_part_bytes(const bse_interp* s);
 int bse_tc_apply_scratch(bse_ctx* ctx, const bse_interp* s, int nchains, __nv_bfloat16* bop, float* part, void* R);
 int bse_apply_scratch(bse_ctx* ctx, const bse_interp* s, int nvec, const void* x, void* y, const ApplyScratch& sc);

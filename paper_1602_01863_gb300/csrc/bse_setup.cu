@@ -539,6 +539,7 @@ int setup_interp_typed(bse_ctx* ctx, bse_interp* s) {
                 BSE_CUDA_TRY(ctx, cudaMemcpy(s->d_pairs, pairs.data(), sizeof(int) * pairs.size(), cudaMemcpyHostToDevice));
                 BSE_CUDA_TRY(ctx, cudaMemcpy(s->d_clist, clist.data(), sizeof(int) * clist.size(), cudaMemcpyHostToDevice));
                 BSE_CUDA_TRY(ctx, cudaMemcpy(s->d_cstart, cstart.data(), sizeof(int) * cstart.size(), cudaMemcpyHostToDevice));
+                TRY(bse_near_tc_prepare(ctx, s, pairs, clist, cstart));
             }
         }
         int* d_offs = nullptr;

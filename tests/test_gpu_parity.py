@@ -42,11 +42,11 @@ def oracle_H(seed, nv, nc, n, nd, method, scheme="8nb", width=1.0):
     return oracle_interp(seed, nv, nc, n, nd, scheme, width).H_dense(method)
 
 
-def gpu_system(ctx, seed, nv, nc, n, nd, method="m1", scheme="8nb", width=1.0, kc_prec=0, vec_prec=0):
+def gpu_system(ctx, seed, nv, nc, n, nd, method="m1", scheme="8nb", width=1.0, kc_prec=0, vec_prec=0, extra=0):
     from paper_1602_01863_gb300 import bse
     m = synth.draw_model(seed, nv, nc)
     co = ctx.bse_build_coarse(m, n, kc_prec)
-    sch = (bse.SCHEME_M3 if method == "m3" else bse.SCHEME_M1) | (bse.NB1 if scheme == "1nb" else 0)
+    sch = (bse.SCHEME_M3 if method == "m3" else bse.SCHEME_M1) | (bse.NB1 if scheme == "1nb" else 0) | extra
     it = ctx.bse_interp_setup(co, nd, sch, width, vec_prec)
     return co, it
 
@@ -110,8 +110,10 @@ def test_apply_h_f64_matches_oracle(ctx, case):
 @pytest.mark.parametrize("nv,nc,method", [(4, 4, "m3"), (4, 6, "m3"), (3, 3, "m3"), (2, 3, "m3"), (4, 4, "m1")])
 def test_apply_h_fp32_matches_oracle(ctx, nv, nc, method):
     """FP32 vectors with complex64 K_c (register-blocked kernels for 3x3, 4x4
-    and 4x6 bands, generic ones otherwise), 3 chains: FP32-level agreement."""
-    co, it = gpu_system(ctx, 13, nv, nc, 3, 2, method, kc_prec=1, vec_prec=1)
+    and 4x6 bands, generic ones otherwise, CUDA-core near field), 3 chains:
+    FP32-level agreement."""
+    from paper_1602_01863_gb300 import bse
+    co, it = gpu_system(ctx, 13, nv, nc, 3, 2, method, kc_prec=1, vec_prec=1, extra=bse.NF_CUDA_CORES)
     H = oracle_H(13, nv, nc, 3, 2, method)
     x = synth.random_vectors(9, (3, it.N)).astype(np.complex64).astype(np.complex128)
     y = apply_gpu(ctx, it, x)
@@ -119,6 +121,32 @@ def test_apply_h_fp32_matches_oracle(ctx, nv, nc, method):
     assert np.abs(y - yr).max() <= 2e-5 * np.abs(yr).max()
     it.free()
     co.free()
+
+
+@pytest.mark.parametrize("nv,nc,n,nd", [(4, 4, 4, 4), (3, 3, 4, 2), (2, 3, 3, 3)])
+def test_tensor_core_near_field(ctx, nv, nc, n, nd):
+    """M3 near field on tcgen05 (TF32 head blocks and y1, z; FP32 accumulation)
+    against the oracle on sampled rows and against the CUDA-core kernel.
+    Bar: TF32 operand rounding (2^-11 relative) amplified by the partial
+    cancellation of y1 against h_head z, a few parts in 1e3 of |near field|."""
+    from paper_1602_01863_gb300 import bse
+    co, it = gpu_system(ctx, 21, nv, nc, n, nd, "m3", kc_prec=1, vec_prec=1)
+    co2, it2 = gpu_system(ctx, 21, nv, nc, n, nd, "m3", kc_prec=1, vec_prec=1, extra=bse.NF_CUDA_CORES)
+    x = synth.random_vectors(4, (2, it.N)).astype(np.complex64).astype(np.complex128)
+    y = apply_gpu(ctx, it, x)
+    y2 = apply_gpu(ctx, it2, x)
+    I = oi.Interp(synth.draw_model(21, nv, nc), n, nd, width=1.0, build_dense_kc=False)
+    rows = np.array([0, 3, it.Nk // 2, it.Nk - 1])
+    for v in range(2):
+        ref_m1 = I.apply_m1_rows(x[v], rows)
+        nf = I.near_field_rows(x[v], rows)
+        got = y[v].reshape(I.Nk, I.t)[rows]
+        err = np.abs(got - (ref_m1 + nf)).max() / np.abs(nf).max()
+        print(f"tensor-core near field, relative error {err:.3e}")
+        assert err <= 5e-3
+    near2 = y2 - y
+    assert np.abs(near2).max() <= 2e-3 * np.abs(y2).max()
+    it.free(); co.free(); it2.free(); co2.free()
 
 
 # ----------------------------------------------------------- Haydock FP64
