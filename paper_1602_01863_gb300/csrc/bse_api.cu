@@ -39,8 +39,8 @@ void free_interp(bse_interp* s) {
                     s->d_hc, s->d_Q, s->d_R, s->d_X, s->d_U, s->d_Bop, s->d_part, s->d_vec[0],
                     s->d_vec[1], s->d_vec[2], s->d_part_dot, s->d_part_nrm, s->d_a, s->d_aim, s->d_b, s->d_stop,
                     s->d_basis, s->d_cgs_part, s->d_cgs_h, s->d_pairs, s->d_clist, s->d_cstart,
-                    s->d_lker, s->d_lgrid, s->d_tw_fwd, s->d_tc_rows, s->d_tc_urow,
-                    s->d_tc_rec, s->d_tc_urec, s->d_tc_uinfo};
+                    s->d_lker, s->d_lgrid, s->d_tw_fwd, s->d_tc_rows, s->d_tc_slots,
+                    s->d_tc_rowstart, s->d_tc_kinfo, s->d_tc_simg};
     for (void* p : ptrs) cudaFree(p);
     bse_tc_release(s);
     if (s->graph) cudaGraphExecDestroy(s->graph);

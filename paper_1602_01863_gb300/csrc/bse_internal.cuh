@@ -155,15 +155,13 @@ struct bse_interp {
     int* d_cstart = nullptr;         // [Ndiv][nslot + 1]
     size_t cell_smem = 0;            // dynamic shared memory of the cell kernel (0: not usable)
     int nf_tc = 0;                   // the tensor-core near field serves this handle
-    size_t nf_tc_smem = 0;
-    int nf_tc_units = 0;             // units (slot pieces) of the near pattern
-    int nf_tc_rec_max = 0;           // largest unit record (ints)
-    int nf_tc_npart = 0;             // most partial sums any unit needs
-    int* d_tc_rows = nullptr;        // staged source rows of every unit: js | corner << 16
-    int2* d_tc_urow = nullptr;       // per unit {first row, rows}
-    int* d_tc_rec = nullptr;         // unit records: schedule and contribution list
-    int2* d_tc_urec = nullptr;       // per unit {record offset, record length} (ints)
-    int2* d_tc_uinfo = nullptr;      // per unit {slot, slot ordinal | first << 16 | last << 17}
+    int nf_tc_nsl = 0;               // slots that reach the cell
+    int nf_tc_nkg = 0;               // their stage-1 K-blocks
+    int* d_tc_rows = nullptr;        // source rows of every slot: js | corner << 16
+    int4* d_tc_slots = nullptr;      // per slot {slot, first K-block, K-blocks, rows}
+    int* d_tc_rowstart = nullptr;    // per slot, first row
+    int* d_tc_kinfo = nullptr;       // per K-block: slot ordinal | K-block in slot << 16
+    unsigned char* d_tc_simg = nullptr;   // near pattern images, 16 KB per K-block
     int nf_force_cuda_cores = 0;     // BSE_NF_CUDA_CORES: keep the CUDA-core near-field kernels
     void* d_hd = nullptr;            // T [n_near]   h_head at dense near offsets
     void* d_Hv = nullptr;            // V [nkc][nrel][nv*nv]
@@ -248,8 +246,7 @@ struct ApplyScratch {
 };
 int bse_launch_near_field(bse_ctx* ctx, const bse_interp* s, int nchains, const void* X, void* U);
 int bse_apply_learned(bse_ctx* ctx, const bse_interp* s, int nchains, const void* psi, void* w, double2* dot);
-int bse_near_tc_prepare(bse_ctx* ctx, bse_interp* s, const std::vector<int>& pairs, const std::vector<int>& clist,
-                        const std::vector<int>& cstart);
+int bse_near_tc_prepare(bse_ctx* ctx, bse_interp* s, const std::vector<std::vector<NearEntry>>& per_slot);
 int bse_near_tc_launch(bse_ctx* ctx, const bse_interp* s, int nchains, const void* X, void* U);
 size_t bse_tc_part_bytes(const bse_interp* s);
 int bse_tc_apply_scratch(bse_ctx* ctx, const bse_interp* s, int nchains, __nv_bfloat16* bop, float* part, void* R);

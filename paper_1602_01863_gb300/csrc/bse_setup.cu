@@ -539,7 +539,6 @@ int setup_interp_typed(bse_ctx* ctx, bse_interp* s) {
                 BSE_CUDA_TRY(ctx, cudaMemcpy(s->d_pairs, pairs.data(), sizeof(int) * pairs.size(), cudaMemcpyHostToDevice));
                 BSE_CUDA_TRY(ctx, cudaMemcpy(s->d_clist, clist.data(), sizeof(int) * clist.size(), cudaMemcpyHostToDevice));
                 BSE_CUDA_TRY(ctx, cudaMemcpy(s->d_cstart, cstart.data(), sizeof(int) * cstart.size(), cudaMemcpyHostToDevice));
-                TRY(bse_near_tc_prepare(ctx, s, pairs, clist, cstart));
             }
         }
         int* d_offs = nullptr;
@@ -563,6 +562,7 @@ int setup_interp_typed(bse_ctx* ctx, bse_interp* s) {
             ctx->err = std::string("M3 set-up kernels: ") + cudaGetErrorString(e);
             return BSE_ERR_CUDA;
         }
+        TRY(bse_near_tc_prepare(ctx, s, per_slot));
     }
     if (c->kc_prec == BSE_PREC_BF16) TRY(bse_tc_prepare(ctx, s));
     return BSE_OK;
