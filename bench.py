@@ -32,6 +32,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_OMEGA = 1000
+# DRAM bytes (read + write) of one near-field launch on this workload from the
+# committed ncu capture, or None when the kernel changed since the capture.
+NEAR_TRAFFIC = None
 
 
 def parse():
@@ -52,6 +55,27 @@ def dist_info():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def rank_seed(rank: int) -> int:
+    """Each rank runs its own independent system of the single-system shape (weak scaling)."""
+    return 2 + rank
+
+
+def slowest_rank_time(t_step: float, ws: int, device=None) -> float:
+    """Max over ranks of the per-rank step time (the job is as slow as its slowest rank)."""
+    if ws == 1:
+        return t_step
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([t_step], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_value(ws: int, chain_steps_per_rank: int, t_max: float) -> float:
+    """Whole-job chain-steps/s: the chain-steps of all ranks over the slowest rank's time."""
+    return ws * chain_steps_per_rank / t_max
 
 
 class Clocks:
@@ -110,6 +134,59 @@ def algorithmic(sysd, nchains, kc_bytes_per_entry, vec_bytes):
     }
 
 
+def near_field_work(nd, width, t, nchains, nkc, nb1=False):
+    """Operation counts of the M3 near field per launch (one Lanczos step, all
+    chains), from the near-pair geometry (integer enumeration, no arithmetic of
+    the method):
+      useful   real flops of the factored form -- stage 1: y1 and z over every
+               (target, source pair) near pair, 2 t real entries per chain;
+               stage 2: for every (target, active target corner, reached slot)
+               the t x t head block applied to y1 and to z, complex, 8 flops per
+               complex multiply-add;
+      issued   real flops of the tensor-core MMAs the kernel issues (stage 1:
+               128 x 32 chains x 32 per K-block; stage 2: 256 x 64 chains x 64
+               per slot, one 128-row half when 16 t <= 128)."""
+    import math
+    R2 = math.floor(width * width * nd * nd + 1e-9)
+    rad = int(math.floor(math.sqrt(R2) + 1e-12))
+    offs = [(a, b, c) for a in range(-rad, rad + 1) for b in range(-rad, rad + 1) for c in range(-rad, rad + 1)
+            if a * a + b * b + c * c <= R2]
+
+    def fdiv(a, n):
+        return (a - a % n) // n
+
+    def wnum(j, l):
+        if nb1:
+            return int(all((2 * j[ax] > nd) == bool((l >> (2 - ax)) & 1) for ax in range(3)))
+        r = 1
+        for ax in range(3):
+            r *= j[ax] if (l >> (2 - ax)) & 1 else nd - j[ax]
+        return r
+
+    subs = [(a, b, c) for a in range(nd) for b in range(nd) for c in range(nd)]
+    rows, pairs, reach = {}, 0, set()
+    for tj, j in enumerate(subs):
+        for o in offs:
+            g = [j[ax] + o[ax] for ax in range(3)]
+            co = [fdiv(x, nd) for x in g]
+            jp = tuple(g[ax] - co[ax] * nd for ax in range(3))
+            for l in range(8):
+                if wnum(jp, l) == 0:
+                    continue
+                slot = tuple(co[ax] + ((l >> (2 - ax)) & 1) for ax in range(3))
+                rows.setdefault(slot, set()).add((tuple(co), jp, l))
+                reach.add((tj, slot))
+                pairs += 1
+    act = [sum(1 for l in range(8) if wnum(j, l)) for j in subs]
+    s2 = sum(act[tj] for tj, _ in reach)
+    useful = nkc * nchains * (pairs * 2 * (2 * t) * 2 + s2 * 2 * t * t * 8)
+    nkg = sum((len(v) + 31) // 32 for v in rows.values())
+    nmh = 2 if 16 * t > 128 else 1
+    issued = nkc * 2 * (nkg * 128 * 32 * nchains * 32 + len(rows) * nmh * 128 * 64 * nchains * 64)
+    return {"useful_flops": float(useful), "issued_flops": float(issued), "near_pairs_per_cell": pairs,
+            "k_blocks_per_cell": nkg, "slots_per_cell": len(rows)}
+
+
 def time_runs(ctx, bse, it, dirs, m, flags, steps, warmup, omega, pref, eta, barrier):
     import torch
     st = torch.cuda.current_stream()
@@ -147,7 +224,7 @@ def run_ours(args):
         if ws > 1:
             dist.barrier()
 
-    sysm = synth.single_system(seed=2 + rank)
+    sysm = synth.single_system(seed=rank_seed(rank))
     m = args.lanczos
     dirs = sysm.pol_dirs
     p = dirs.shape[0]
@@ -166,13 +243,9 @@ def run_ours(args):
     ms, res, eps_mixed = time_runs(ctx, bse, it, dirs, m, bse.USE_GRAPH, args.steps, args.warmup, omega, pref, eta, barrier)
     clk = clocks.stop()
     t_step = ms / 1e3 / args.steps
-    t_max = t_step
-    if ws > 1:
-        tt = torch.tensor([t_step], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
+    t_max = slowest_rank_time(t_step, ws, dev)
     chain_steps = p * m
-    value = ws * chain_steps / t_max
+    value = job_value(ws, chain_steps, t_max)
 
     # ---------------- per-kernel device times (CUDA events on the launching stream)
     ctx.bse_haydock_run([it], [p], dirs, m, bse.PROFILE)
@@ -184,14 +257,20 @@ def run_ours(args):
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     # FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop x max SM clock
-    fp32_peak = 152 * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
-    if dom in alg and "bytes" in alg[dom]:
+    # TF32 dense tensor peak: the measured BF16 burst figure x the nominal TF32 / BF16 ratio (1.1 / 2.25)
+    tf32_peak = float(peaks.get("bf16_tflops", 1900.0)) * 1.1 / 2.25
+    nfw = near_field_work(sysm.n_div, 1.0, info["nv"] * info["nc"], p, sysm.nk_coarse)
+    if dom == "near_field":
+        achieved = nfw["useful_flops"] / (kt[dom][0] * 1e-3) / 1e12
+        roof = {"bound": "tensor", "kernel": "k_near_tc (M3 near field, tcgen05 TF32)", "achieved": achieved,
+                "peak": tf32_peak, "unit": "TFLOP/s", "frac": achieved / tf32_peak, "traffic": NEAR_TRAFFIC,
+                "peak_source": f"{peak_src} bf16 burst x nominal TF32/BF16 ratio 1.1/2.25",
+                "flops": "useful flops of the factored near field (stage 1 y1, z; stage 2 head blocks)",
+                "issued_tflops": nfw["issued_flops"] / (kt[dom][0] * 1e-3) / 1e12}
+    else:
         achieved = alg[dom]["bytes"] / (kt[dom][0] * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src}
-    else:
-        roof = {"bound": "alu", "kernel": dom, "achieved": None, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": None, "traffic": None, "peak_source": "152 SM x 128 FP32 lanes x 2 x 2070 MHz"}
     kc = alg["kc_apply"]
     kc_gbs = kc["bytes"] / (kt["kc_apply"][0] * 1e-3) / 1e9
     kernels = {k: {"ms": round(v[0], 5), "launches": v[1]} for k, v in kt.items()}

@@ -119,47 +119,130 @@ __global__ void __launch_bounds__(256) k_restrict(
     (void)stop;
 }
 
-// Register-blocked restrict (FP32, compile-time band counts): one thread per
-// (corner l, sub-point js) candidate of the target coarse point; x = f conj(Dv)
-// psi Dc^T is formed row by row (Dc in registers), summed per thread, then
-// over the block in a fixed order (two stages through shared memory).
+// ------------------------------------------------ staged restrict and prolong
+// Both kernels take one coarse point (restrict) or one coarse cell (prolong)
+// per CTA and walk its eight corners l.  For each corner the active
+// (sub-point, corner) pairs (f != 0) come from per-CTA lists built with a warp
+// ballot; their d rows, and the psi rows (restrict) or the R and u rows
+// (prolong), are staged in shared memory by cp.async, double-buffered across
+// corners, each row padded to an odd number of complex entries so that a warp
+// reading one row per lane touches every bank at most twice.  Thread
+// (chain c, item s) = (tid / 64, tid % 64) computes its pair from shared
+// memory; the d tables are read from HBM once for all chains.
+// Limits: N_div <= 64, <= 4 chains (= 256 threads / 64).
+
+constexpr int odd_pad(int x) { return x | 1; }
+
+__device__ __forceinline__ void cpa8(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cpa4(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cpa_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cpa_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Active sub-points of every corner: cnt[l], list[l][i] = js (ascending),
+// pos[l][js] = i or -1.  Warps 0-7 build corner l = warp.
+__device__ __forceinline__ void corner_lists(int nd, int nb1, int* cnt, int* list, signed char* pos) {
+    const int Ndiv = nd * nd * nd, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < 8) {
+        const int l = warp;
+        int base = 0;
+        for (int j0 = 0; j0 < Ndiv; j0 += 32) {
+            const int js = j0 + lane;
+            const bool act = js < Ndiv && interp_active(js, l, nd, nb1);
+            const unsigned m = __ballot_sync(0xffffffffu, act);
+            const int idx = base + __popc(m & ((1u << lane) - 1u));
+            if (js < Ndiv) pos[l * 64 + js] = act ? (signed char)idx : (signed char)-1;
+            if (act) list[l * 64 + idx] = js;
+            base += __popc(m);
+        }
+        if (lane == 0) cnt[l] = base;
+    }
+}
+
+template <int NV, int NC>
+__host__ __device__ constexpr int restrict_st_buf(int nchains) {
+    return 64 * (odd_pad(NV * NV) + odd_pad(NC * NC)) + nchains * 64 * odd_pad(NV * NC);
+}
+template <int NV, int NC>
+size_t restrict_st_smem(int nchains) {
+    const size_t a = 2 * (size_t)restrict_st_buf<NV, NC>(nchains), b = 256 * (size_t)odd_pad(NV * NC);
+    return sizeof(float2) * std::max(a, b);
+}
+
+// Restrict (Eq. matmul1 gathered by Eq. ordersums), one CTA per target coarse
+// point k~: x(k, l) = f conj(Dv) psi Dc^T for every active pair of the source
+// cells k~ - l, written to X, and Q(k~) = sum of the x, summed over the 64 item
+// threads of each chain in a fixed order.
 template <int NV, int NC, bool OUT_BF16>
-__global__ void __launch_bounds__(256) k_restrict_rb(
+__global__ void __launch_bounds__(256) k_restrict_st(
     const float2* __restrict__ psi, const float2* __restrict__ Dv, const float2* __restrict__ Dc, int n, int nd,
     int nb1, int nchains, int N, int Nc, float2* __restrict__ Q, __nv_bfloat16* __restrict__ Bop, int ldk,
     float2* __restrict__ X) {
-    constexpr int t = NV * NC, tp = t + 1;
-    constexpr int NG = 256 / t;                                // row groups of the block reduction
-    __shared__ float2 red[256 * tp];
-    __shared__ float2 part[NG * t];
-    const int Ndiv = nd * nd * nd;
-    const int ic = blockIdx.x, tid = threadIdx.x;
+    constexpr int t = NV * NC, RV = NV * NV, RC = NC * NC;
+    constexpr int RVp = odd_pad(RV), RCp = odd_pad(RC), TP = odd_pad(t);
+    extern __shared__ float2 st_sm[];
+    __shared__ int cnt[8];
+    __shared__ int list[8 * 64];
+    __shared__ signed char pos[8 * 64];
+    const int Ndiv = nd * nd * nd, nk = N / t;
+    const int buf = restrict_st_buf<NV, NC>(nchains);
+    const int ic = blockIdx.x, tid = threadIdx.x, c = tid >> 6, s = tid & 63;
     const Int3 i = unflat3(ic, n);
-    for (int ch = 0; ch < nchains; ++ch) {
-        float2 acc[NV][NC];
+    corner_lists(nd, nb1, cnt, list, pos);
+    __syncthreads();
+    auto src_cell = [&](int l) { return flat3(i.a - ((l >> 2) & 1), i.b - ((l >> 1) & 1), i.c - (l & 1), n); };
+    auto stage = [&](int l, float2* b) {
+        const int m = cnt[l];
+        const size_t cell0 = (size_t)src_cell(l) * Ndiv;
+        float2* dv = b;
+        float2* dc = dv + 64 * RVp;
+        float2* ps = dc + 64 * RCp;
+        for (int q = tid; q < m * RV; q += 256) {
+            const int it = q / RV, k = q - it * RV;
+            cpa8(dv + it * RVp + k, Dv + ((cell0 + list[l * 64 + it]) * 8 + l) * RV + k);
+        }
+        for (int q = tid; q < m * RC; q += 256) {
+            const int it = q / RC, k = q - it * RC;
+            cpa8(dc + it * RCp + k, Dc + ((cell0 + list[l * 64 + it]) * 8 + l) * RC + k);
+        }
+        for (int ch = 0; ch < nchains; ++ch)
+            for (int q = tid; q < m * t; q += 256) {
+                const int it = q / t, e = q - it * t;
+                cpa8(ps + (ch * 64 + it) * TP + e, psi + (size_t)ch * N + (cell0 + list[l * 64 + it]) * t + e);
+            }
+    };
+    float2 acc[t];
 #pragma unroll
-        for (int a = 0; a < NV; ++a)
-#pragma unroll
-            for (int b = 0; b < NC; ++b) acc[a][b] = make_float2(0.f, 0.f);
-        for (int cand = tid; cand < 8 * Ndiv; cand += 256) {
-            const int l = cand / Ndiv, js = cand - l * Ndiv;
+    for (int e = 0; e < t; ++e) acc[e] = make_float2(0.f, 0.f);
+    stage(0, st_sm);
+    cpa_commit();
+    for (int l = 0; l < 8; ++l) {
+        if (l + 1 < 8) {
+            stage(l + 1, st_sm + ((l + 1) & 1) * buf);
+            cpa_commit();
+            cpa_wait1();
+        } else {
+            cpa_wait0();
+        }
+        __syncthreads();
+        const float2* b = st_sm + (l & 1) * buf;
+        if (c < nchains && s < cnt[l]) {
+            const int js = list[l * 64 + s];
             const float f = interp_weight_f(js, l, nd, nb1);
-            if (f == 0.f) continue;
-            const int src = flat3(i.a - ((l >> 2) & 1), i.b - ((l >> 1) & 1), i.c - (l & 1), n);
-            const size_t kd = (size_t)src * Ndiv + js;
-            const float2* dv = Dv + (kd * 8 + l) * NV * NV;
-            const float2* dcp = Dc + (kd * 8 + l) * NC * NC;
-            const float2* ps = psi + (size_t)ch * N + kd * t;
-            float2 dc[NC][NC];
-#pragma unroll
-            for (int a = 0; a < NC; ++a)
-#pragma unroll
-                for (int b = 0; b < NC; ++b) dc[a][b] = dcp[a * NC + b];
+            const float2* dv = b + s * RVp;
+            const float2* dc = b + 64 * RVp + s * RCp;
+            const float2* ps = b + 64 * (RVp + RCp) + (c * 64 + s) * TP;
             float2 x[NV][NC];
 #pragma unroll
             for (int a = 0; a < NV; ++a)
 #pragma unroll
-                for (int b = 0; b < NC; ++b) x[a][b] = make_float2(0.f, 0.f);
+                for (int bb = 0; bb < NC; ++bb) x[a][bb] = make_float2(0.f, 0.f);
 #pragma unroll
             for (int vp = 0; vp < NV; ++vp) {
                 float2 pr[NC];
@@ -168,13 +251,14 @@ __global__ void __launch_bounds__(256) k_restrict_rb(
                 float2 t1[NC];                                  // t1[n4] = sum_c' psi[vp][c'] Dc[n4][c']
 #pragma unroll
                 for (int n4 = 0; n4 < NC; ++n4) {
-                    float2 s = make_float2(0.f, 0.f);
+                    float2 sacc = make_float2(0.f, 0.f);
 #pragma unroll
                     for (int cp = 0; cp < NC; ++cp) {
-                        s.x = fmaf(pr[cp].x, dc[n4][cp].x, fmaf(-pr[cp].y, dc[n4][cp].y, s.x));
-                        s.y = fmaf(pr[cp].x, dc[n4][cp].y, fmaf(pr[cp].y, dc[n4][cp].x, s.y));
+                        const float2 d = dc[n4 * NC + cp];
+                        sacc.x = fmaf(pr[cp].x, d.x, fmaf(-pr[cp].y, d.y, sacc.x));
+                        sacc.y = fmaf(pr[cp].x, d.y, fmaf(pr[cp].y, d.x, sacc.y));
                     }
-                    t1[n4] = s;
+                    t1[n4] = sacc;
                 }
 #pragma unroll
                 for (int n3 = 0; n3 < NV; ++n3) {
@@ -186,153 +270,228 @@ __global__ void __launch_bounds__(256) k_restrict_rb(
                     }
                 }
             }
-            float2* xo = X ? X + (((size_t)ch * (N / t) + kd) * 8 + l) * t : nullptr;
+            const size_t kd = (size_t)src_cell(l) * Ndiv + js;
+            float2* xo = X + (((size_t)c * nk + kd) * 8 + l) * t;
 #pragma unroll
             for (int a = 0; a < NV; ++a)
 #pragma unroll
-                for (int b = 0; b < NC; ++b) {
-                    const float2 v = make_float2(x[a][b].x * f, x[a][b].y * f);
-                    if (xo) xo[a * NC + b] = v;
-                    acc[a][b].x += v.x;
-                    acc[a][b].y += v.y;
+                for (int bb = 0; bb < NC; ++bb) {
+                    const float2 v = make_float2(x[a][bb].x * f, x[a][bb].y * f);
+                    if (X) xo[a * NC + bb] = v;
+                    acc[a * NC + bb].x += v.x;
+                    acc[a * NC + bb].y += v.y;
                 }
         }
+        __syncthreads();
+    }
+    // Q(k~): fixed-order sum over the 64 item threads of each chain
+    float2* red = st_sm;
 #pragma unroll
-        for (int a = 0; a < NV; ++a)
-#pragma unroll
-            for (int b = 0; b < NC; ++b) red[tid * tp + a * NC + b] = acc[a][b];
-        __syncthreads();
-        if (tid < NG * t) {
-            const int e = tid % t, g = tid / t;
-            float2 s = make_float2(0.f, 0.f);
-            for (int r = g; r < 256; r += NG) {
-                const float2 v = red[r * tp + e];
-                s.x += v.x;
-                s.y += v.y;
-            }
-            part[g * t + e] = s;
+    for (int e = 0; e < t; ++e) red[tid * TP + e] = acc[e];
+    __syncthreads();
+    for (int idx = tid; idx < nchains * t; idx += 256) {
+        const int ch = idx / t, e = idx - ch * t;
+        float2 sum = make_float2(0.f, 0.f);
+        for (int r = 0; r < 64; ++r) {
+            const float2 v = red[(ch * 64 + r) * TP + e];
+            sum.x += v.x;
+            sum.y += v.y;
         }
-        __syncthreads();
-        if (tid < t) {
-            float2 s = part[tid];
-            for (int g = 1; g < NG; ++g) {
-                const float2 v = part[g * t + tid];
-                s.x += v.x;
-                s.y += v.y;
-            }
-            const int row = ic * t + tid;
-            if (!OUT_BF16) {
-                Q[(size_t)ch * Nc + row] = s;
-            } else {
-                const __nv_bfloat16 rh = __float2bfloat16_rn(s.x), ih = __float2bfloat16_rn(s.y);
-                Bop[(size_t)ch * ldk + row] = rh;
-                Bop[(size_t)(nchains + ch) * ldk + row] = ih;
-                Bop[(size_t)(2 * nchains + ch) * ldk + row] = __float2bfloat16_rn(s.x - __bfloat162float(rh));
-                Bop[(size_t)(3 * nchains + ch) * ldk + row] = __float2bfloat16_rn(s.y - __bfloat162float(ih));
-            }
+        const int row = ic * t + e;
+        if (!OUT_BF16) {
+            Q[(size_t)ch * Nc + row] = sum;
+        } else {
+            const __nv_bfloat16 rh = __float2bfloat16_rn(sum.x), ih = __float2bfloat16_rn(sum.y);
+            Bop[(size_t)ch * ldk + row] = rh;
+            Bop[(size_t)(nchains + ch) * ldk + row] = ih;
+            Bop[(size_t)(2 * nchains + ch) * ldk + row] = __float2bfloat16_rn(sum.x - __bfloat162float(rh));
+            Bop[(size_t)(3 * nchains + ch) * ldk + row] = __float2bfloat16_rn(sum.y - __bfloat162float(ih));
         }
-        __syncthreads();
     }
 }
 
-// Register-blocked prolong + diagonal (FP32): one thread per (chain, dense
-// point); per corner T = M conj(Dc) is formed row by row (Dc in registers)
-// and Dv^T T accumulated; block partials of <psi, w> as in k_prolong.
+template <int NV, int NC>
+__host__ __device__ constexpr int prolong_st_buf(int nchains, bool near) {
+    return 64 * (odd_pad(NV * NV) + odd_pad(NC * NC)) + nchains * odd_pad(NV * NC) +
+           (near ? nchains * 64 * odd_pad(NV * NC) : 0);
+}
+// Epilogue rows (psi [chain][sub-point][TP] complex, dE [sub-point][TP] real) in
+// complex units, and where they go: buffer 0 when they fit (it is free while
+// corner 7 runs from buffer 1), else after both buffers.
+template <int NV, int NC>
+__host__ __device__ constexpr int prolong_st_eps(int nchains) {
+    return nchains * 64 * odd_pad(NV * NC) + 32 * odd_pad(NV * NC);
+}
+template <int NV, int NC>
+__host__ __device__ constexpr int prolong_st_eps_off(int nchains, bool near) {
+    return prolong_st_eps<NV, NC>(nchains) <= prolong_st_buf<NV, NC>(nchains, near) ? 0 : 2 * prolong_st_buf<NV, NC>(nchains, near);
+}
+template <int NV, int NC>
+size_t prolong_st_smem(int nchains, bool near) {
+    const size_t a = 2 * (size_t)prolong_st_buf<NV, NC>(nchains, near);
+    const size_t b = (size_t)prolong_st_eps_off<NV, NC>(nchains, near) + prolong_st_eps<NV, NC>(nchains);
+    return sizeof(float2) * std::max(a, b);
+}
+constexpr int kProlongMaxCtas = BSE_MAX_VEC_BLOCKS;
+
+// Prolong + diagonal (Eqs. matmul3, bse1), one CTA per coarse cell (grid-strided):
+// w(k) = dE psi(k) + (1/N_div) sum_l f Dv^T (R(k~_l) + u(k, l)) conj(Dc) for the
+// cell's sub-points k; w leaves through shared memory in coalesced rows; the
+// CTA's FP64 partials of <psi, w> per chain go to part[chain][blockIdx.x].
 template <int NV, int NC, bool NEAR>
-__global__ void __launch_bounds__(BSE_VEC_THREADS) k_prolong_rb(
+__global__ void __launch_bounds__(256) k_prolong_st(
     const float2* __restrict__ R, const float2* __restrict__ Unf, const float2* __restrict__ Dv,
     const float2* __restrict__ Dc, const float* __restrict__ dE, const float2* __restrict__ psi, int n, int nd,
     int nb1, int nchains, int N, int Nc, float2* __restrict__ W, double2* __restrict__ part) {
-    constexpr int t = NV * NC;
-    __shared__ double2 red[BSE_MAX_CHAINS][BSE_VEC_THREADS];
-    const int Ndiv = nd * nd * nd;
-    const int nk = N / t;
+    constexpr int t = NV * NC, RV = NV * NV, RC = NC * NC;
+    constexpr int RVp = odd_pad(RV), RCp = odd_pad(RC), TP = odd_pad(t);
+    extern __shared__ float2 st_sm[];
+    __shared__ int cnt[8];
+    __shared__ int list[8 * 64];
+    __shared__ signed char pos[8 * 64];
+    __shared__ double2 dred[256];
+    const int Ndiv = nd * nd * nd, nk = N / t, nkc = nk / Ndiv;
+    const int buf = prolong_st_buf<NV, NC>(nchains, NEAR);
+    const int tid = threadIdx.x, c = tid >> 6, js = tid & 63;
     const float inv_ndiv = 1.f / (float)Ndiv;
-    double2 dot[BSE_MAX_CHAINS];
-#pragma unroll
-    for (int c = 0; c < BSE_MAX_CHAINS; ++c) dot[c] = make_double2(0.0, 0.0);
-    const long long total = (long long)nchains * nk;
-    for (long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x; gid < total;
-         gid += (long long)gridDim.x * blockDim.x) {
-        const int ch = (int)(gid / nk), kd = (int)(gid - (long long)ch * nk);
-        const int cell = kd / Ndiv, js = kd - cell * Ndiv;
+    corner_lists(nd, nb1, cnt, list, pos);
+    __syncthreads();
+    double2 dot = make_double2(0.0, 0.0);
+    for (int cell = blockIdx.x; cell < nkc; cell += gridDim.x) {
         const Int3 ci = unflat3(cell, n);
-        float2 s[NV][NC];
+        const size_t cell0 = (size_t)cell * Ndiv;
+        auto stage = [&](int l, float2* b) {
+            const int m = cnt[l];
+            float2* dv = b;
+            float2* dc = dv + 64 * RVp;
+            float2* rr = dc + 64 * RCp;
+            float2* uu = rr + nchains * TP;
+            for (int q = tid; q < m * RV; q += 256) {
+                const int it = q / RV, k = q - it * RV;
+                cpa8(dv + it * RVp + k, Dv + ((cell0 + list[l * 64 + it]) * 8 + l) * RV + k);
+            }
+            for (int q = tid; q < m * RC; q += 256) {
+                const int it = q / RC, k = q - it * RC;
+                cpa8(dc + it * RCp + k, Dc + ((cell0 + list[l * 64 + it]) * 8 + l) * RC + k);
+            }
+            const int cc = flat3(ci.a + ((l >> 2) & 1), ci.b + ((l >> 1) & 1), ci.c + (l & 1), n);
+            for (int q = tid; q < nchains * t; q += 256) {
+                const int ch = q / t, e = q - ch * t;
+                cpa8(rr + ch * TP + e, R + (size_t)ch * Nc + (size_t)cc * t + e);
+            }
+            if (NEAR)
+                for (int ch = 0; ch < nchains; ++ch)
+                    for (int q = tid; q < m * t; q += 256) {
+                        const int it = q / t, e = q - it * t;
+                        cpa8(uu + (ch * 64 + it) * TP + e,
+                             Unf + (((size_t)ch * nk + cell0 + list[l * 64 + it]) * 8 + l) * t + e);
+                    }
+        };
+        float2* eps_ps = st_sm + prolong_st_eps_off<NV, NC>(nchains, NEAR);
+        float* eps_de = reinterpret_cast<float*>(eps_ps + nchains * 64 * TP);
+        auto stage_epilogue = [&]() {
+            for (int ch = 0; ch < nchains; ++ch)
+                for (int q = tid; q < Ndiv * t; q += 256) {
+                    const int j = q / t, e = q - j * t;
+                    cpa8(eps_ps + (ch * 64 + j) * TP + e, psi + (size_t)ch * N + cell0 * t + q);
+                }
+            for (int q = tid; q < Ndiv * t; q += 256) {
+                const int j = q / t, e = q - j * t;
+                cpa4(eps_de + j * TP + e, dE + cell0 * t + q);
+            }
+        };
+        float2 sacc[NV][NC];
 #pragma unroll
         for (int a = 0; a < NV; ++a)
 #pragma unroll
-            for (int b = 0; b < NC; ++b) s[a][b] = make_float2(0.f, 0.f);
+            for (int bb = 0; bb < NC; ++bb) sacc[a][bb] = make_float2(0.f, 0.f);
+        stage(0, st_sm);
+        cpa_commit();
         for (int l = 0; l < 8; ++l) {
-            const float f = interp_weight_f(js, l, nd, nb1);
-            if (f == 0.f) continue;
-            const int cc = flat3(ci.a + ((l >> 2) & 1), ci.b + ((l >> 1) & 1), ci.c + (l & 1), n);
-            const float2* dv = Dv + ((size_t)kd * 8 + l) * NV * NV;
-            const float2* dcp = Dc + ((size_t)kd * 8 + l) * NC * NC;
-            const float2* rr = R + (size_t)ch * Nc + (size_t)cc * t;
-            const float2* uu = NEAR ? Unf + (((size_t)ch * nk + kd) * 8 + l) * t : nullptr;
-            float2 dc[NC][NC];
+            if (l + 1 < 8) stage(l + 1, st_sm + ((l + 1) & 1) * buf);
+            else stage_epilogue();
+            cpa_commit();
+            cpa_wait1();
+            __syncthreads();
+            const float2* b = st_sm + (l & 1) * buf;
+            const int p = js < Ndiv ? (int)pos[l * 64 + js] : -1;
+            if (c < nchains && p >= 0) {
+                const float f = interp_weight_f(js, l, nd, nb1);
+                const float2* dv = b + p * RVp;
+                const float2* dc = b + 64 * RVp + p * RCp;
+                const float2* rr = b + 64 * (RVp + RCp) + c * TP;
+                const float2* uu = b + 64 * (RVp + RCp) + nchains * TP + (c * 64 + p) * TP;
 #pragma unroll
-            for (int a = 0; a < NC; ++a)
-#pragma unroll
-                for (int b = 0; b < NC; ++b) dc[a][b] = dcp[a * NC + b];
-#pragma unroll
-            for (int n1 = 0; n1 < NV; ++n1) {
-                float2 m[NC];
-#pragma unroll
-                for (int n2 = 0; n2 < NC; ++n2) {
-                    m[n2] = rr[n1 * NC + n2];
-                    if (NEAR) { const float2 u = uu[n1 * NC + n2]; m[n2].x += u.x; m[n2].y += u.y; }
-                }
-                float2 tr[NC];                                  // tr[c] = sum_n2 m[n2] conj(Dc[n2][c])
-#pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    float2 a = make_float2(0.f, 0.f);
+                for (int n1 = 0; n1 < NV; ++n1) {
+                    float2 m[NC];
 #pragma unroll
                     for (int n2 = 0; n2 < NC; ++n2) {
-                        a.x = fmaf(m[n2].x, dc[n2][c].x, fmaf(m[n2].y, dc[n2][c].y, a.x));
-                        a.y = fmaf(m[n2].y, dc[n2][c].x, fmaf(-m[n2].x, dc[n2][c].y, a.y));
+                        m[n2] = rr[n1 * NC + n2];
+                        if (NEAR) { const float2 u = uu[n1 * NC + n2]; m[n2].x += u.x; m[n2].y += u.y; }
                     }
-                    tr[c] = make_float2(a.x * f, a.y * f);
-                }
+                    float2 tr[NC];                              // tr[c] = sum_n2 m[n2] conj(Dc[n2][c])
 #pragma unroll
-                for (int v = 0; v < NV; ++v) {
-                    const float2 d = dv[n1 * NV + v];
+                    for (int cc = 0; cc < NC; ++cc) {
+                        float2 a = make_float2(0.f, 0.f);
 #pragma unroll
-                    for (int c = 0; c < NC; ++c) {
-                        s[v][c].x = fmaf(d.x, tr[c].x, fmaf(-d.y, tr[c].y, s[v][c].x));
-                        s[v][c].y = fmaf(d.x, tr[c].y, fmaf(d.y, tr[c].x, s[v][c].y));
+                        for (int n2 = 0; n2 < NC; ++n2) {
+                            const float2 d = dc[n2 * NC + cc];
+                            a.x = fmaf(m[n2].x, d.x, fmaf(m[n2].y, d.y, a.x));
+                            a.y = fmaf(m[n2].y, d.x, fmaf(-m[n2].x, d.y, a.y));
+                        }
+                        tr[cc] = make_float2(a.x * f, a.y * f);
+                    }
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) {
+                        const float2 d = dv[n1 * NV + v];
+#pragma unroll
+                        for (int cc = 0; cc < NC; ++cc) {
+                            sacc[v][cc].x = fmaf(d.x, tr[cc].x, fmaf(-d.y, tr[cc].y, sacc[v][cc].x));
+                            sacc[v][cc].y = fmaf(d.x, tr[cc].y, fmaf(d.y, tr[cc].x, sacc[v][cc].y));
+                        }
                     }
                 }
             }
+            __syncthreads();
         }
-        const size_t base = (size_t)kd * t;
-        double2 dd = make_double2(0.0, 0.0);
+        cpa_wait0();
+        __syncthreads();
+        // w = dE psi + s / N_div; <psi, w> in FP64; w written over the psi row
+        if (c < nchains && js < Ndiv) {
+            float2* row = eps_ps + (c * 64 + js) * TP;
+            const float* de = eps_de + js * TP;
+            float dre = 0.f, dim = 0.f;                         // the row's t products in FP32, rows summed in FP64
 #pragma unroll
-        for (int a = 0; a < NV; ++a)
+            for (int a = 0; a < NV; ++a)
 #pragma unroll
-            for (int b = 0; b < NC; ++b) {
-                const int e = a * NC + b;
-                const float2 p = psi[(size_t)ch * N + base + e];
-                const float de = dE[base + e];
-                const float2 w = make_float2(fmaf(p.x, de, s[a][b].x * inv_ndiv), fmaf(p.y, de, s[a][b].y * inv_ndiv));
-                W[(size_t)ch * N + base + e] = w;
-                dd.x += (double)p.x * w.x + (double)p.y * w.y;
-                dd.y += (double)p.x * w.y - (double)p.y * w.x;
+                for (int bb = 0; bb < NC; ++bb) {
+                    const int e = a * NC + bb;
+                    const float2 pv = row[e];
+                    const float d = de[e];
+                    const float2 w = make_float2(fmaf(pv.x, d, sacc[a][bb].x * inv_ndiv), fmaf(pv.y, d, sacc[a][bb].y * inv_ndiv));
+                    row[e] = w;
+                    dre = fmaf(pv.x, w.x, fmaf(pv.y, w.y, dre));
+                    dim = fmaf(pv.x, w.y, fmaf(-pv.y, w.x, dim));
+                }
+            dot.x += (double)dre;
+            dot.y += (double)dim;
+        }
+        __syncthreads();
+        for (int ch = 0; ch < nchains; ++ch)
+            for (int q = tid; q < Ndiv * t; q += 256) {
+                const int j = q / t, e = q - j * t;
+                W[(size_t)ch * N + cell0 * t + q] = eps_ps[(ch * 64 + j) * TP + e];
             }
-#pragma unroll
-        for (int c = 0; c < BSE_MAX_CHAINS; ++c)
-            if (c == ch) { dot[c].x += dd.x; dot[c].y += dd.y; }
-    }
-#pragma unroll
-    for (int c = 0; c < BSE_MAX_CHAINS; ++c) red[c][threadIdx.x] = dot[c];
-    __syncthreads();
-    for (int st = BSE_VEC_THREADS / 2; st > 0; st >>= 1) {
-        if (threadIdx.x < st)
-#pragma unroll
-            for (int c = 0; c < BSE_MAX_CHAINS; ++c) red[c][threadIdx.x] = cadd(red[c][threadIdx.x], red[c][threadIdx.x + st]);
         __syncthreads();
     }
-    if (threadIdx.x < nchains) part[(size_t)threadIdx.x * BSE_MAX_VEC_BLOCKS + blockIdx.x] = red[threadIdx.x][0];
+    // per-chain partial: fixed-order tree over the chain's 64 threads
+    dred[tid] = dot;
+    __syncthreads();
+    for (int st = 32; st > 0; st >>= 1) {
+        if ((tid & 63) < st) dred[tid] = cadd(dred[tid], dred[tid + st]);
+        __syncthreads();
+    }
+    if (tid < nchains * 64 && (tid & 63) == 0) part[(size_t)(tid >> 6) * BSE_MAX_VEC_BLOCKS + blockIdx.x] = dred[tid];
 }
 
 // ------------------------------------------------- K_c apply on CUDA cores
@@ -952,6 +1111,69 @@ __global__ void __launch_bounds__(BSE_VEC_THREADS) k_cgs_update(const typename C
     if (threadIdx.x == 0) part[(size_t)ch * BSE_MAX_VEC_BLOCKS + blockIdx.x] = s.x;
 }
 
+// FP32 vectors, two complex entries per float4 (N even).  The vector update is
+// FP32 arithmetic (the vectors are FP32); ||w||^2 is summed per thread in FP32
+// over its few entries and across threads and blocks in FP64, in a fixed order.
+// GB300 runs FP64 at 1/64 of the FP32 rate, so per-entry FP64 work would bound
+// these kernels.
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// w <- w - a_i psi_i - b_i psi_{i-1}; block partials of ||w||^2 (every chain in one pass).
+__global__ void __launch_bounds__(256) k_lanczos_axpy4(float4* __restrict__ W, const float4* __restrict__ psi,
+                                                       const float4* __restrict__ psi_prev, const double* __restrict__ a,
+                                                       const double* __restrict__ b, int step, int m, int N4,
+                                                       int nchains, double* __restrict__ part,
+                                                       const int* __restrict__ stop) {
+    __shared__ double red[BSE_MAX_CHAINS][8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int ch = 0; ch < nchains; ++ch) {
+        const bool run = !stop[ch];
+        const float ai = (float)a[ch * m + step], bi = (float)b[ch * (m + 1) + step];
+        float nrm = 0.f;
+        if (run)
+            for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < N4; g += gridDim.x * blockDim.x) {
+                const size_t o = (size_t)ch * N4 + g;
+                const float4 w = W[o], p = psi[o], q = psi_prev[o];
+                float4 r;
+                r.x = fmaf(-bi, q.x, fmaf(-ai, p.x, w.x));
+                r.y = fmaf(-bi, q.y, fmaf(-ai, p.y, w.y));
+                r.z = fmaf(-bi, q.z, fmaf(-ai, p.z, w.z));
+                r.w = fmaf(-bi, q.w, fmaf(-ai, p.w, w.w));
+                W[o] = r;
+                nrm = fmaf(r.x, r.x, fmaf(r.y, r.y, fmaf(r.z, r.z, fmaf(r.w, r.w, nrm))));
+            }
+        const double ws = warp_sum_d((double)nrm);
+        if (lane == 0) red[ch][warp] = ws;
+    }
+    __syncthreads();
+    if (threadIdx.x < nchains && !stop[threadIdx.x]) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[threadIdx.x][w];
+        part[(size_t)threadIdx.x * BSE_MAX_VEC_BLOCKS + blockIdx.x] = s;
+    }
+}
+
+// psi_{i+1} = w / b_{i+1} (written over psi_{i-1}), also into the basis when kept.
+__global__ void __launch_bounds__(256) k_lanczos_scale4(const float4* __restrict__ W, float4* __restrict__ out,
+                                                        const double* __restrict__ b, int step, int m, int N4,
+                                                        int nchains, float4* __restrict__ basis, int mb,
+                                                        const int* __restrict__ stop) {
+    for (int ch = 0; ch < nchains; ++ch) {
+        if (stop[ch]) continue;
+        const float inv = (float)(1.0 / b[ch * (m + 1) + step + 1]);
+        for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < N4; g += gridDim.x * blockDim.x) {
+            const float4 w = W[(size_t)ch * N4 + g];
+            const float4 v = make_float4(w.x * inv, w.y * inv, w.z * inv, w.w * inv);
+            out[(size_t)ch * N4 + g] = v;
+            if (basis) basis[((size_t)ch * mb + step + 1) * N4 + g] = v;
+        }
+    }
+}
+
 // b_{i+1} = sqrt(sum partials); breakdown when b_{i+1} < 1e-12 max_j |a_j|.
 __global__ void k_reduce_b(const double* __restrict__ part, int nblk, int step, int m, const double* __restrict__ a,
                            double* __restrict__ b, int* __restrict__ stop) {
@@ -1068,6 +1290,28 @@ inline int vec_blocks(long long N) {
     return (int)std::min<long long>(std::max<long long>(b, 1), BSE_MAX_VEC_BLOCKS);
 }
 
+// Raise a kernel's dynamic shared-memory limit when a launch needs more than the
+// current one (by default 48 KB less the kernel's static shared memory); only
+// ever raised: handles of different sizes share the attribute.
+template <typename K>
+void ensure_smem(K kernel, size_t bytes) {
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, kernel) == cudaSuccess && (size_t)fa.maxDynamicSharedSizeBytes < bytes)
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// The staged FP32 restrict / prolong kernels serve 3x3, 4x4 and 4x6 bands with N_div <= 64.
+inline bool staged_bands(const bse_interp* s) {
+    return s->vec_prec == BSE_PREC_F32 && s->Ndiv <= 64 &&
+           ((s->nv == 3 && s->nc == 3) || (s->nv == 4 && s->nc == 4) || (s->nv == 4 && s->nc == 6));
+}
+
+// Number of <psi, w> block partials one H application leaves in the dot buffer.
+inline int dot_blocks(const bse_interp* s) {
+    if (!s->learned && staged_bands(s)) return std::min(s->co->nkc, kProlongMaxCtas);
+    return vec_blocks(s->N);
+}
+
 // Restrict: register-blocked FP32 kernel for 3x3 and 4x4 bands, generic otherwise.
 template <typename T>
 void launch_restrict(bse_ctx* ctx, const bse_interp* s, int nchains, const void* psi, void* Q, __nv_bfloat16* bop,
@@ -1080,19 +1324,25 @@ void launch_restrict(bse_ctx* ctx, const bse_interp* s, int nchains, const void*
         const float2* p = (const float2*)psi;
         const float2* dv = (const float2*)s->d_Dv;
         const float2* dc = (const float2*)s->d_Dc;
-#define BSE_RB_RESTRICT(NV_, NC_)                                                                                   \
-    if (s->nv == NV_ && s->nc == NC_) {                                                                             \
-        if (bf)                                                                                                     \
-            k_restrict_rb<NV_, NC_, true><<<c->nkc, 256, 0, st>>>(p, dv, dc, s->n, s->nd, s->nb1, nchains, s->N,   \
-                                                                 c->Nc, nullptr, bop, c->ldk, (float2*)X);          \
-        else                                                                                                        \
-            k_restrict_rb<NV_, NC_, false><<<c->nkc, 256, 0, st>>>(p, dv, dc, s->n, s->nd, s->nb1, nchains, s->N,  \
-                                                                  c->Nc, (float2*)Q, nullptr, 0, (float2*)X);       \
+#define BSE_ST_RESTRICT(NV_, NC_)                                                                                   \
+    if (s->nv == NV_ && s->nc == NC_ && s->Ndiv <= 64) {                                                            \
+        const size_t smem = restrict_st_smem<NV_, NC_>(nchains);                                                    \
+        if (bf) {                                                                                                   \
+            ensure_smem(k_restrict_st<NV_, NC_, true>, smem);                                                       \
+            k_restrict_st<NV_, NC_, true><<<c->nkc, 256, smem, st>>>(p, dv, dc, s->n, s->nd, s->nb1, nchains, s->N,\
+                                                                    c->Nc, nullptr, bop, c->ldk, (float2*)X);       \
+        } else {                                                                                                    \
+            ensure_smem(k_restrict_st<NV_, NC_, false>, smem);                                                      \
+            k_restrict_st<NV_, NC_, false><<<c->nkc, 256, smem, st>>>(p, dv, dc, s->n, s->nd, s->nb1, nchains,     \
+                                                                     s->N, c->Nc, (float2*)Q, nullptr, 0,           \
+                                                                     (float2*)X);                                   \
+        }                                                                                                           \
         return;                                                                                                     \
     }
-        BSE_RB_RESTRICT(3, 3)
-        BSE_RB_RESTRICT(4, 4)
-#undef BSE_RB_RESTRICT
+        BSE_ST_RESTRICT(3, 3)
+        BSE_ST_RESTRICT(4, 4)
+        BSE_ST_RESTRICT(4, 6)
+#undef BSE_ST_RESTRICT
     }
     if (bf)
         k_restrict<T, true><<<c->nkc, 256, 0, st>>>((const V*)psi, (const V*)s->d_Dv, (const V*)s->d_Dc, s->n, s->nd,
@@ -1114,23 +1364,28 @@ void launch_prolong(bse_ctx* ctx, const bse_interp* s, int nchains, const void* 
     const int nb = vec_blocks(s->N);
     const bool m3 = U != nullptr;
     if constexpr (std::is_same<T, float>::value) {
-#define BSE_RB_PROLONG(NV_, NC_)                                                                                     \
-    if (s->nv == NV_ && s->nc == NC_) {                                                                              \
-        if (m3)                                                                                                      \
-            k_prolong_rb<NV_, NC_, true><<<nb, BSE_VEC_THREADS, 0, st>>>(                                            \
+#define BSE_ST_PROLONG(NV_, NC_)                                                                                     \
+    if (s->nv == NV_ && s->nc == NC_ && s->Ndiv <= 64) {                                                             \
+        const size_t smem = prolong_st_smem<NV_, NC_>(nchains, m3);                                                  \
+        const int g = std::min(c->nkc, kProlongMaxCtas);                                                             \
+        if (m3) {                                                                                                    \
+            ensure_smem(k_prolong_st<NV_, NC_, true>, smem);                                                         \
+            k_prolong_st<NV_, NC_, true><<<g, 256, smem, st>>>(                                                      \
                 (const float2*)R, (const float2*)U, (const float2*)s->d_Dv, (const float2*)s->d_Dc,                  \
                 (const float*)s->d_dE, (const float2*)psi, s->n, s->nd, s->nb1, nchains, s->N, c->Nc, (float2*)W,    \
                 dot);                                                                                                \
-        else                                                                                                         \
-            k_prolong_rb<NV_, NC_, false><<<nb, BSE_VEC_THREADS, 0, st>>>(                                           \
+        } else {                                                                                                     \
+            ensure_smem(k_prolong_st<NV_, NC_, false>, smem);                                                        \
+            k_prolong_st<NV_, NC_, false><<<g, 256, smem, st>>>(                                                     \
                 (const float2*)R, nullptr, (const float2*)s->d_Dv, (const float2*)s->d_Dc, (const float*)s->d_dE,    \
                 (const float2*)psi, s->n, s->nd, s->nb1, nchains, s->N, c->Nc, (float2*)W, dot);                     \
+        }                                                                                                            \
         return;                                                                                                      \
     }
-        BSE_RB_PROLONG(3, 3)
-        BSE_RB_PROLONG(4, 4)
-        BSE_RB_PROLONG(4, 6)
-#undef BSE_RB_PROLONG
+        BSE_ST_PROLONG(3, 3)
+        BSE_ST_PROLONG(4, 4)
+        BSE_ST_PROLONG(4, 6)
+#undef BSE_ST_PROLONG
     }
     if (m3)
         k_prolong<T, true><<<nb, BSE_VEC_THREADS, 0, st>>>((const V*)R, (const V*)U, (const V*)s->d_Dv,
@@ -1247,6 +1502,9 @@ int enqueue_chains(bse_ctx* ctx, bse_interp* s, int nch, const double* d_dirs, d
     V* W = (V*)s->d_vec[2];
     V* basis = reorth ? (V*)s->d_basis : nullptr;
     const int mb = s->basis_m;
+    // FP32 vectors with an even length: float4 update kernels, one float4 per thread and chain
+    const bool vec4 = std::is_same<T, float>::value && (N % 2) == 0;
+    const int nb4 = (int)std::min<long long>(std::max<long long>((N / 2 + 255) / 256, 1), BSE_MAX_VEC_BLOCKS);
     cudaMemsetAsync(s->d_stop, 0, sizeof(int) * BSE_MAX_CHAINS, st);
     // psi_1 = P / ||P|| in B, psi_0 = 0 in A
     k_dipole_start<T><<<nb, BSE_VEC_THREADS, 0, st>>>(s->d_P, d_dirs, N, nch, B, s->d_part_nrm);
@@ -1256,8 +1514,12 @@ int enqueue_chains(bse_ctx* ctx, bse_interp* s, int nch, const double* d_dirs, d
         int rc = apply_h_typed<T>(ctx, s, nch, B, W, prof);
         if (rc != BSE_OK) return rc;
         Timer tm(ctx, prof, KC_LANCZOS);
-        k_reduce_a<<<nch, 256, 0, st>>>(s->d_part_dot, nb, i, m, s->d_a, s->d_aim, s->d_stop);
-        k_lanczos_axpy<T><<<nb, BSE_VEC_THREADS, 0, st>>>(W, B, A, s->d_a, s->d_b, i, m, N, nch, s->d_part_nrm, s->d_stop);
+        k_reduce_a<<<nch, 256, 0, st>>>(s->d_part_dot, dot_blocks(s), i, m, s->d_a, s->d_aim, s->d_stop);
+        if (vec4)
+            k_lanczos_axpy4<<<nb4, 256, 0, st>>>((float4*)W, (const float4*)B, (const float4*)A, s->d_a, s->d_b, i, m,
+                                                 N / 2, nch, s->d_part_nrm, s->d_stop);
+        else
+            k_lanczos_axpy<T><<<nb, BSE_VEC_THREADS, 0, st>>>(W, B, A, s->d_a, s->d_b, i, m, N, nch, s->d_part_nrm, s->d_stop);
         if (reorth) {
             for (int ch = 0; ch < nch; ++ch)
                 for (int pass = 0; pass < 2; ++pass) {
@@ -1267,8 +1529,12 @@ int enqueue_chains(bse_ctx* ctx, bse_interp* s, int nch, const double* d_dirs, d
                     k_cgs_update<T><<<nb, BSE_VEC_THREADS, 0, st>>>(basis, W, s->d_cgs_h, i + 1, mb, N, ch, s->d_part_nrm);
                 }
         }
-        k_reduce_b<<<nch, 256, 0, st>>>(s->d_part_nrm, nb, i, m, s->d_a, s->d_b, s->d_stop);
-        k_lanczos_scale<T><<<nb, BSE_VEC_THREADS, 0, st>>>(W, A, s->d_b, i, m, N, nch, basis, mb, s->d_stop);
+        k_reduce_b<<<nch, 256, 0, st>>>(s->d_part_nrm, (vec4 && !reorth) ? nb4 : nb, i, m, s->d_a, s->d_b, s->d_stop);
+        if (vec4)
+            k_lanczos_scale4<<<nb4, 256, 0, st>>>((const float4*)W, (float4*)A, s->d_b, i, m, N / 2, nch, (float4*)basis,
+                                                  mb, s->d_stop);
+        else
+            k_lanczos_scale<T><<<nb, BSE_VEC_THREADS, 0, st>>>(W, A, s->d_b, i, m, N, nch, basis, mb, s->d_stop);
         std::swap(A, B);
     }
     return BSE_OK;
@@ -1329,7 +1595,7 @@ int run_chains_typed(bse_ctx* ctx, bse_interp* s, int nch, const double* pol_dir
         return BSE_ERR_CUDA;
     }
     if (status != 0) {
-        ctx->err = "a bounded device wait in the tensor-core K_c apply gave up";
+        ctx->err = bse_timeout_message(status);
         cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st);
         return BSE_ERR_TIMEOUT;
     }
@@ -1375,7 +1641,7 @@ int bse_apply_once(bse_ctx* ctx, bse_interp* s, int nvec, const void* x, void* y
     cudaMemcpy(&status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost);
     if (status) {
         cudaMemset(ctx->d_status, 0, sizeof(int));
-        ctx->err = "a bounded device wait in the tensor-core K_c apply gave up";
+        ctx->err = bse_timeout_message(status);
         return BSE_ERR_TIMEOUT;
     }
     return BSE_OK;
@@ -1487,7 +1753,7 @@ int bse_run_batch(bse_ctx* ctx, bse_interp* const* sys, int nsys, const int* npo
     }
     if (status != 0) {
         cudaMemset(ctx->d_status, 0, sizeof(int));
-        ctx->err = "a bounded device wait in the tensor-core K_c apply gave up";
+        ctx->err = bse_timeout_message(status);
         return BSE_ERR_TIMEOUT;
     }
     int warn = BSE_OK;

@@ -112,7 +112,7 @@ struct bse_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;          // created by the context (caller passed NULL)
     std::string err;
-    int* d_status = nullptr;          // device status word: bit 0 = bounded wait gave up
+    int* d_status = nullptr;          // device status word: bit value 1 / 2 = a bounded wait gave up in the K_c apply / near field
     double kt_ms[KC_COUNT] = {0, 0, 0, 0, 0};
     long long kt_n[KC_COUNT] = {0, 0, 0, 0, 0};
     int sm_count = 0;
@@ -157,6 +157,7 @@ struct bse_interp {
     int nf_tc = 0;                   // the tensor-core near field serves this handle
     int nf_tc_nsl = 0;               // slots that reach the cell
     int nf_tc_nkg = 0;               // their stage-1 K-blocks
+    int nf_tc_nrows = 0;             // their source rows (all slots)
     int* d_tc_rows = nullptr;        // source rows of every slot: js | corner << 16
     int4* d_tc_slots = nullptr;      // per slot {slot, first K-block, K-blocks, rows}
     int* d_tc_rowstart = nullptr;    // per slot, first row
@@ -211,6 +212,13 @@ struct bse_interp {
     } while (0)
 
 int bse_alloc(bse_ctx* ctx, void** p, size_t bytes, const char* what);
+
+// Status word bits raised by bounded device waits: 1 = tensor-core K_c apply,
+// 2 = tensor-core near field.
+inline const char* bse_timeout_message(int status) {
+    if (status & 2) return "a bounded device wait in the tensor-core near field gave up";
+    return "a bounded device wait in the tensor-core K_c apply gave up";
+}
 
 // setup kernels (bse_setup.cu)
 int bse_setup_coarse_device(bse_ctx* ctx, bse_coarse* c);

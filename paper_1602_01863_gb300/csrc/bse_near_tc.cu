@@ -11,9 +11,8 @@
 // or 1) with the gathered source rows X_s.  S_s is the same for every cell
 // (translation invariance of the near pattern), so set-up writes it once as
 // TF32 images of 32-row K-blocks; the kernel gathers X_s (all chains, columns
-// (chain, e, re|im)) transposed into shared memory with cp.async and issues
-//   D1 [128 = (y1|z, target)] x [32 * chains] += S_s[., K-block] * X_s[K-block]^T
-// through a three-stage ring.
+// (chain, e, re|im)) transposed into shared memory and issues
+//   D1 [128 = (y1|z, target)] x [32 * chains] += S_s[., K-block] * X_s[K-block]^T.
 // Stage 2 (per slot): D1 is read back from TMEM into the B operand
 //   B_s[(chain, k), (Y|Z, e', re|im)]  = y1(k, s), z(k, s)
 // and, with the real form
@@ -23,8 +22,26 @@
 //   D2 [256 = (l, e, re|im)] x [64 * chains] += Ahat_s [256 x 64] * B_s^T.
 // tcgen05.mma kind::tf32 (10-bit mantissa, FP32 range: y1 and h_head z nearly
 // cancel in u, which BF16 would not resolve), FP32 accumulators in TMEM.
+//
+// Warp roles (768 threads, one CTA per coarse cell):
+//   warps 4-7      MMA issuer (warp 4, lane 0, also TMEM owner) and D1 -> B
+//                  converters (TMEM lane quarters 0-3); after each slot the four
+//                  warps convert D1 and meet at a named barrier, after which the
+//                  issuer goes on, so this hand-off never sleeps on an mbarrier
+//   warps 8-15     stage-1 producers: the S image by one bulk copy, the X rows by
+//                  4-byte cp.async gathers laid out so that a warp's 32 stores
+//                  hit 32 distinct banks; each warp keeps the whole ring in
+//                  flight and signals a stage once its copies have landed
+//   warps 0-3, 16-23  Ahat writers (per slot, in two 128-row halves), with the
+//                  slot's head factors staged one slot ahead
+// The stage-2 MMAs of slot i - 1 are issued between the stage-1 K-blocks of slot
+// i, so the tensor pipe works on one while the producers refill the ring; D1 and
+// B are single-buffered (TMEM holds D2, 2 x 64 x chains columns, and D1,
+// 32 x chains), Ahat is released half by half.
 // Constraints: t <= 16, N_div <= 64, FP32 vectors, <= 3 chains per launch.
-// Every wait is bounded.
+// Every wait is bounded; on expiry the kernel raises bit 1 of the status word,
+// every role leaves its loop, the MMAs and copies in flight are drained and
+// TMEM is freed.
 #include <cuda.h>
 
 #include <algorithm>
@@ -41,28 +58,34 @@ constexpr int NT_STAGES = 3;                 // stage-1 ring depth
 constexpr int S_BYTES = 128 * NT_KB * 4;     // one S image K-block: 16 KB
 constexpr int A_KB = NT_M * 128;             // one 32-element K-block of A: 32 KB
 constexpr int A_BYTES = 2 * A_KB;            // 64 KB per slot
-constexpr int NT_THREADS = 512;
+constexpr int NT_THREADS = 768;
 constexpr int NT_TMEM_COLS = 512;
-constexpr long long NT_WAIT_CYCLES = 4000000000LL;
+constexpr int W_C0 = 4, W_CN = 4;            // MMA issuer (warp 4, lane 0) + converters (warp % 4 = TMEM lane quarter)
+constexpr int W_P0 = 8, W_PN = 8;            // producers: warp W_P0 + p stages rows 4p .. 4p + 3
+constexpr int W_A1 = 16;                     // Ahat writers: warps 0-3 and 16-23
+constexpr int W_AN = W_C0 + (NT_THREADS / 32 - W_A1);
+constexpr int NT_A = 32 * W_AN;              // Ahat writer threads
+constexpr int NT_AMAX = 3;                   // items per writer thread and slot (8 t ceil(t / 2) <= 1024)
+static_assert(NT_A * NT_AMAX >= 1024, "Ahat items per slot");
+constexpr long long NT_WAIT_CYCLES = 400000000LL;   // ~0.2 s; a whole launch takes well under 10 ms
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(su32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(dst)), "l"(src) : "memory");
-}
 __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(su32(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+// every group but the newest NT_STAGES - 1 landed (the K-block NT_STAGES - 1 behind the newest)
+__device__ __forceinline__ void cp_async_wait_lag() { asm volatile("cp.async.wait_group %0;" ::"n"(NT_STAGES - 1) : "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ uint32_t f2tf32(float v) {
     uint32_t u;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(v));
     return u;
 }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // Byte offset of 32-bit element (row r, column k) of a K-major operand stored as
 // K-blocks of 32 elements (128-byte rows), each block `rows` x 128 B with the
@@ -75,21 +98,67 @@ __host__ __device__ __forceinline__ uint32_t sw128(int r, int k, int rows) {
 __device__ __forceinline__ void bar_init(uint32_t b, uint32_t c) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b), "r"(c) : "memory");
 }
+__device__ __forceinline__ void bar_arrive(uint32_t b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(b) : "memory");
+}
+__device__ __forceinline__ void bar_arrive_tx(uint32_t b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ bool bar_try(uint32_t b, uint32_t parity) {
     uint32_t ok;
     asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
                  : "=r"(ok) : "r"(b), "r"(parity) : "memory");
     return ok != 0;
 }
-__device__ __forceinline__ bool bar_wait(uint32_t b, uint32_t parity, int* status) {
+// Non-blocking test of a phase.
+__device__ __forceinline__ bool bar_test(uint32_t b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok) : "r"(b), "r"(parity) : "memory");
+    return ok != 0;
+}
+// Bounded wait: false when another role gave up (abort flag) or the clock
+// budget ran out (raises status bit 1 and the abort flag).
+__device__ __forceinline__ bool bar_wait(uint32_t b, uint32_t parity, int* status, volatile int* abort_flag) {
     const long long t0 = clock64();
     while (!bar_try(b, parity)) {
+        if (*abort_flag) return false;
         if (clock64() - t0 > NT_WAIT_CYCLES) {
             atomicOr(status, 2);
+            *abort_flag = 1;
             return false;
         }
     }
     return true;
+}
+// Bounded spin on the non-blocking test, for the roles on the critical path
+// (MMA issuer, converters): no suspension, so no wake-up latency.
+__device__ __forceinline__ bool bar_spin(uint32_t b, uint32_t parity, int* status, volatile int* abort_flag) {
+    long long t0 = -1;
+    for (int it = 1;; ++it) {
+        if (bar_test(b, parity)) return true;
+        if ((it & 63) == 0) {
+            if (*abort_flag) return false;
+            const long long now = clock64();
+            if (t0 < 0) t0 = now;
+            else if (now - t0 > NT_WAIT_CYCLES) {
+                atomicOr(status, 2);
+                *abort_flag = 1;
+                return false;
+            }
+        }
+    }
+}
+// Wait that ignores the abort flag (drain paths: copies and MMAs in flight always finish).
+__device__ __forceinline__ void bar_drain(uint32_t b, uint32_t parity, int* status) {
+    const long long t0 = clock64();
+    while (!bar_try(b, parity)) {
+        if (clock64() - t0 > NT_WAIT_CYCLES) { atomicOr(status, 2); return; }
+    }
+}
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
 }
 __device__ __forceinline__ uint64_t desc_sw128(uint32_t addr) {
     return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
@@ -122,14 +191,10 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Pack four values rounded to TF32 into one 16-byte chunk.
-__device__ __forceinline__ uint4 pack_tf32(float a, float b, float c, float d) {
-    uint4 u;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u.x) : "f"(a));
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u.y) : "f"(b));
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u.z) : "f"(c));
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u.w) : "f"(d));
-    return u;
+__device__ __forceinline__ void writers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(NT_A) : "memory"); }
+__device__ __forceinline__ void converters_sync() { asm volatile("bar.sync 2, %0;" ::"n"(32 * W_CN) : "memory"); }
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(su32(dst)), "l"(src) : "memory");
 }
 
 // Shared-memory bytes of one head-factor buffer: Hv, Hc of the 8 target corners
@@ -138,227 +203,322 @@ __host__ __device__ __forceinline__ int hb_bytes(int nv, int nc) {
     return ((8 * (nv * nv + nc * nc) * 8 + 32) + 15) & ~15;
 }
 
+// Pack four values rounded to TF32 into one 16-byte chunk.
+__device__ __forceinline__ uint4 pack_tf32(float a, float b, float c, float d) {
+    return make_uint4(f2tf32(a), f2tf32(b), f2tf32(c), f2tf32(d));
+}
+
+// Shared-memory layout (bytes from the 1024-aligned base) for `nch` chains.
+struct NtLayout {
+    int N1, N2, b_off, ring_off, stage_bytes, tab_off;
+    __host__ __device__ NtLayout(int nch) {
+        N1 = 32 * nch;
+        N2 = 64 * nch;
+        b_off = A_BYTES;                                  // Ahat: [2 K-blocks][256 rows][128 B]
+        ring_off = b_off + 2 * N2 * 128;                  // B: [2 K-blocks (Y, Z)][N2 rows][128 B]
+        stage_bytes = S_BYTES + N1 * 128;                 // ring stage: S K-block | X K-block
+        tab_off = ring_off + NT_STAGES * stage_bytes;     // head-factor buffers [2], then slot tables
+    }
+};
+
 // Slot table entry {slot, first K-block, K-blocks, source rows} and per-K-block
 // info (slot ordinal | K-block in slot << 16) are staged in shared memory.
 __global__ void __launch_bounds__(NT_THREADS, 1) k_near_tc(
     const float* __restrict__ X, const int* __restrict__ rows, const int4* __restrict__ slots,
-    const int* __restrict__ rowstart, const int* __restrict__ kinfo, int nsl, int nkg,
+    const int* __restrict__ rowstart, const int* __restrict__ kinfo, int nsl, int nkg, int nrows,
     const unsigned char* __restrict__ Simg, const float2* __restrict__ Hv, const float2* __restrict__ Hc,
     const float* __restrict__ hc, int n, int nd, int nv, int nc, int nb1, int smin, int ns1, int rmin, int nr1,
     int nch, float2* __restrict__ U, int* __restrict__ status) {
+    // an earlier launch on this context gave up a wait: skip (the host reports BSE_ERR_TIMEOUT)
+    if (*reinterpret_cast<volatile int*>(status) & 2) return;
     extern __shared__ unsigned char raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~(uintptr_t)1023);
-    __shared__ uint64_t bar_s[NT_STAGES], bar_d1, bar_mma2, bar_drain;
+    __shared__ uint64_t bar_full[NT_STAGES], bar_sfull[NT_STAGES], bar_empty[NT_STAGES];
+    __shared__ uint64_t bar_d1_full, bar_a_full[2], bar_a_free[2], bar_d2;
     __shared__ uint32_t tmem_sh;
-    __shared__ int abort_flag;
+    __shared__ int abort_sh;
+    volatile int* abort_flag = &abort_sh;
     const int t = nv * nc, Ndiv = nd * nd * nd, nslot = ns1 * ns1 * ns1, nrel = nr1 * nr1 * nr1;
-    const int nk = n * n * n * Ndiv, th = (t + 1) >> 1, hbb = hb_bytes(nv, nc), nitem = 8 * t * th;
-    const int N1 = 32 * nch, N2 = 64 * nch, stage_bytes = S_BYTES + N1 * 128;
+    const int nk = n * n * n * Ndiv, th = (t + 1) >> 1;
+    // D2 rows (l, e, re|im) = 2 (l t + e) + re|im; the second 128-row half holds
+    // anything only when 16 t > 128
+    const int nmh = (16 * t > 128) ? 2 : 1;
+    const NtLayout lay(nch);
+    const int N1 = lay.N1, N2 = lay.N2;
     const int cell = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    unsigned char* A2 = sm;                                     // [A_BYTES]   Ahat_s
-    unsigned char* B2 = sm + A_BYTES;                           // [2][N2 x 128 B]  B_s, Y and Z K-blocks
-    unsigned char* ring = B2 + 2 * N2 * 128;                    // [NT_STAGES][S K-block | X K-block]
-    unsigned char* hbuf = ring + NT_STAGES * stage_bytes;       // [2][hbb]
-    int4* aidx = reinterpret_cast<int4*>(hbuf + 2 * hbb);       // [nitem] A-tile item tables
-    int4* s_sl = aidx + nitem;                                  // [nsl]
+    unsigned char* A2 = sm;
+    unsigned char* B2 = sm + lay.b_off;
+    unsigned char* ring = sm + lay.ring_off;
+    const int hbb = hb_bytes(nv, nc);
+    unsigned char* hbuf = sm + lay.tab_off;                     // [2][hbb]  head factors, slot parity
+    int4* s_sl = reinterpret_cast<int4*>(hbuf + 2 * hbb);       // [nsl]
     int* s_rs = reinterpret_cast<int*>(s_sl + nsl);             // [nsl]
     int* s_ki = s_rs + nsl;                                     // [nkg]
     int* scell = s_ki + nkg;                                    // [nslot][8] source cells
+    unsigned short* s_rows = reinterpret_cast<unsigned short*>(scell + nslot * 8);   // [nrows] js | corner << 8
     const Int3 ci = unflat3(cell, n);
     for (int i = tid; i < nsl; i += NT_THREADS) { s_sl[i] = slots[i]; s_rs[i] = rowstart[i]; }
     for (int i = tid; i < nkg; i += NT_THREADS) s_ki[i] = kinfo[i];
+    for (int i = tid; i < nrows; i += NT_THREADS) {
+        const int code = rows[i];
+        s_rows[i] = (unsigned short)((code & 0xFF) | ((code >> 16) << 8));
+    }
     for (int i = tid; i < nslot * 8; i += NT_THREADS) {
         const int s = i >> 3, l = i & 7;
         const Int3 so = unflat3(s, ns1);
         scell[i] = flat3(ci.a + so.a + smin - ((l >> 2) & 1), ci.b + so.b + smin - ((l >> 1) & 1),
                          ci.c + so.c + smin - (l & 1), n);
     }
-    // A-tile items: {Hv offsets of e'0 | e'1 << 16, Hc offsets likewise, chunk offsets of the re | im rows,
-    // corner | (e'1 exists) << 8}
-    for (int it = tid; it < nitem; it += NT_THREADS) {
-        const int l = it / (t * th), e = (it / th) % t, qp = it % th;
-        const int n1 = e / nc, n2 = e % nc, ep0 = 2 * qp, ep1 = 2 * qp + 1, has1 = ep1 < t;
-        const int e1 = has1 ? ep1 : ep0;
-        const int row = (l * t + e) * 2, kq = 4 * qp;
-        aidx[it] = make_int4((l * nv * nv + n1 * nv + ep0 / nc) | ((l * nv * nv + n1 * nv + e1 / nc) << 16),
-                             (l * nc * nc + n2 * nc + ep0 % nc) | ((l * nc * nc + n2 * nc + e1 % nc) << 16),
-                             (int)sw128(row, kq, NT_M) | ((int)sw128(row + 1, kq, NT_M) << 16), l | (has1 << 8));
-    }
     // zero the operands once: padding rows / columns stay zero for the whole kernel
-    for (int i = tid; i < (int)((ring + NT_STAGES * stage_bytes - sm) / 16); i += NT_THREADS)
-        reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < lay.tab_off / 16; i += NT_THREADS) reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
+    fence_async_smem();
     if (tid == 0) {
-        for (int q = 0; q < NT_STAGES; ++q) bar_init(su32(&bar_s[q]), 1);
-        bar_init(su32(&bar_d1), 1);
-        bar_init(su32(&bar_mma2), 1);
-        bar_init(su32(&bar_drain), 1);
-        abort_flag = 0;
+        for (int q = 0; q < NT_STAGES; ++q) {
+            bar_init(su32(&bar_full[q]), W_PN);                // one arrival per producer warp
+            bar_init(su32(&bar_sfull[q]), 1);
+            bar_init(su32(&bar_empty[q]), 1);
+        }
+        bar_init(su32(&bar_d1_full), 1);
+        for (int h = 0; h < 2; ++h) {
+            bar_init(su32(&bar_a_full[h]), W_AN);
+            bar_init(su32(&bar_a_free[h]), 1);
+        }
+        bar_init(su32(&bar_d2), 1);
+        abort_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) {
+    if (warp == W_C0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_sh)), "r"(NT_TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    tc_fence_before();
     __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    tc_fence_after();
     const uint32_t tmem = tmem_sh, tD1 = tmem + (uint32_t)(2 * N2);
 
-    // stage-1 gather map: warp w stages rows w and w + 16 of a K-block, lane = (e, re|im)
-    const int twot = 2 * t;
-    int rc[2];                                                  // row codes of the next K-block to stage
-    auto load_codes = [&](int kg) {
-        const int i = s_ki[kg] & 0xFFFF, kb = s_ki[kg] >> 16;
-        const int R = s_sl[i].w;
+    if (warp >= W_C0 && warp < W_P0) {
+        // ---------------------------------------- MMA issuer and D1 -> B converters
+        const int quarter = warp & 3;
+        const int L = quarter * 32 + lane, yz = L >> 6, j = L & 63;
+        unsigned char* dst = B2 + yz * (N2 * 128);
+        const uint32_t id1 = idesc_tf32(N1), id2 = idesc_tf32(N2);
+        const uint32_t a0 = su32(A2), b0 = su32(B2);
+        const int n2mma = 8 * nmh;                               // stage-2 MMAs per slot: (half, Y|Z, k-step)
+        bool ok = true;
+        int kg = 0;
+        for (int i = 0; i <= nsl; ++i) {
+            if (warp == W_C0) {
+                if (lane == 0 && ok) {
+                    // phase i: stage 1 of slot i (i < nsl) with stage 2 of slot i - 1 (i > 0) spread between its K-blocks
+                    const int nkb = (i < nsl) ? s_sl[i].z : 0;
+                    int s2 = 0;                                  // next stage-2 MMA
+                    // stage-2 MMAs up to `upto`; between K-blocks (force = false) a half
+                    // whose Ahat is not ready yet is left for later instead of waited for
+                    auto issue_s2 = [&](int upto, bool force) {
+                        while (ok && s2 < upto) {
+                            const int mh = s2 >> 3, yzb = (s2 >> 2) & 1, kk = s2 & 3;
+                            if ((s2 & 7) == 0) {
+                                const uint32_t ab = su32(&bar_a_full[mh]), par = (uint32_t)((i - 1) & 1);
+                                if (!force && !bar_test(ab, par)) return;
+                                ok = bar_spin(ab, par, status, abort_flag);
+                                if (!ok) return;
+                                tc_fence_after();
+                            }
+                            mma(tmem + (uint32_t)(mh * N2), desc_sw128(a0 + yzb * A_KB + mh * (A_KB / 2) + kk * 32),
+                                desc_sw128(b0 + yzb * N2 * 128 + kk * 32), id2, (i > 1 || yzb > 0 || kk > 0) ? 1u : 0u);
+                            ++s2;
+                            if ((s2 & 7) == 0) commit(su32(&bar_a_free[mh]));
+                        }
+                    };
+                    for (int kb = 0; kb < nkb && ok; ++kb, ++kg) {
+                        const int q = kg % NT_STAGES;
+                        const uint32_t par = (uint32_t)((kg / NT_STAGES) & 1);
+                        ok = bar_spin(su32(&bar_full[q]), par, status, abort_flag) &&
+                             bar_spin(su32(&bar_sfull[q]), par, status, abort_flag);
+                        if (!ok) break;
+                        fence_async_smem();                      // the producers' cp.async writes, for the async proxy
+                        tc_fence_after();
+                        const uint32_t sa = su32(ring + q * lay.stage_bytes), sb = sa + S_BYTES;
 #pragma unroll
-        for (int rr = 0; rr < 2; ++rr) {
-            const int r = kb * NT_KB + warp + 16 * rr;
-            rc[rr] = r < R ? __ldg(rows + s_rs[i] + r) : -1;
-        }
-    };
-    auto prefetch = [&](int kg) {
-        const int i = s_ki[kg] & 0xFFFF, kb = s_ki[kg] >> 16, q = kg % NT_STAGES;
-        const int4 si = s_sl[i];
-        const int s = si.x;
-        unsigned char* Sq = ring + q * stage_bytes;
-        unsigned char* Bq = Sq + S_BYTES;
-        const unsigned char* src = Simg + (size_t)(si.y + kb) * S_BYTES;
-        for (int c = tid; c < S_BYTES / 16; c += NT_THREADS) cp_async16(Sq + 16 * c, src + 16 * c);
-        if (lane < twot) {
-#pragma unroll
-            for (int rr = 0; rr < 2; ++rr) {
-                if (rc[rr] < 0) continue;
-                const int js = rc[rr] & 0xFFFF, l = rc[rr] >> 16, kk = warp + 16 * rr;
-                const size_t rowsrc = (((size_t)scell[s * 8 + l] * Ndiv + js) * 8 + l) * t;
-                for (int ch = 0; ch < nch; ++ch)
-                    cp_async4(Bq + sw128(ch * 32 + lane, kk, N1), X + ((size_t)ch * nk * 8 * t + rowsrc) * 2 + lane);
-            }
-        }
-        if (kb == 0) {                                          // first K-block of a slot: its head factors
-            const Int3 so = unflat3(s, ns1);
-            const int oa = so.a + smin, ob = so.b + smin, oc = so.c + smin;
-            float2* hvS = reinterpret_cast<float2*>(hbuf + (i & 1) * hbb);
-            float2* hmS = hvS + 8 * nv * nv;
-            float* hcS = reinterpret_cast<float*>(hmS + 8 * nc * nc);
-            const int nvv = nv * nv, ncc = nc * nc, per = nvv + ncc + 1;
-            for (int j = tid; j < 8 * per; j += NT_THREADS) {
-                const int l = j / per, w = j - l * per;
-                const int l1 = (l >> 2) & 1, l2 = (l >> 1) & 1, l3 = l & 1;
-                const int kt = flat3(ci.a + l1, ci.b + l2, ci.c + l3, n);
-                const int r = ((oa - l1 - rmin) * nr1 + (ob - l2 - rmin)) * nr1 + (oc - l3 - rmin);
-                if (w < nvv) cp_async8(hvS + l * nvv + w, Hv + ((size_t)kt * nrel + r) * nvv + w);
-                else if (w < nvv + ncc) cp_async8(hmS + l * ncc + (w - nvv), Hc + ((size_t)kt * nrel + r) * ncc + (w - nvv));
-                else cp_async4(hcS + l, hc + r);
-            }
-        }
-    };
-
-    const uint32_t id1 = idesc_tf32(N1), id2 = idesc_tf32(N2);
-    load_codes(0);
-    prefetch(0);
-    cp_async_commit();
-    if (nkg > 1) load_codes(1);
-    for (int kg = 0; kg < nkg; ++kg) {
-        const int i = s_ki[kg] & 0xFFFF, kb = s_ki[kg] >> 16, q = kg % NT_STAGES;
-        const int4 si = s_sl[i];
-        // the stage of K-block kg + 1 was read by the MMAs of K-block kg + 1 - NT_STAGES
-        if (kg + 1 < nkg) {
-            if (kg + 1 >= NT_STAGES) {
-                const int qn = (kg + 1) % NT_STAGES, use = (kg + 1 - NT_STAGES) / NT_STAGES;
-                if (!bar_wait(su32(&bar_s[qn]), (uint32_t)(use & 1), status)) abort_flag = 1;
-            }
-            prefetch(kg + 1);
-            if (kg + 2 < nkg) load_codes(kg + 2);
-        }
-        cp_async_commit();
-        cp_async_wait1();                                       // this thread's copies of K-block kg landed
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (abort_flag) break;
-        // stage 1: D1 (+)= S_s[., K-block] * X[K-block]^T
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t sa = su32(ring + q * stage_bytes), sb = sa + S_BYTES;
-#pragma unroll
-            for (int kk = 0; kk < NT_KB / 8; ++kk)
-                mma(tD1, desc_sw128(sa + kk * 32), desc_sw128(sb + kk * 32), id1, (kb > 0 || kk > 0) ? 1u : 0u);
-            commit(su32(&bar_s[q]));
-        }
-        if (kb == si.z - 1) {
-            // slot end: Ahat_s, then D1 complete -> B_s -> stage 2.  Ahat and B_s are
-            // rewritten here: the previous slot's stage-2 MMAs must be done.
-            if (tid == 0) {
-                commit(su32(&bar_d1));
-                if (i > 0 && !bar_wait(su32(&bar_mma2), (uint32_t)((i - 1) & 1), status)) abort_flag = 1;
-            }
-            __syncthreads();
-            if (abort_flag) break;
-            {
-                // Ahat_s: item (l, e, pair of e') writes one 16-byte chunk to four rows
-                const float2* hvS = reinterpret_cast<const float2*>(hbuf + (i & 1) * hbb);
-                const float2* hmS = hvS + 8 * nv * nv;
-                const float* hcS = reinterpret_cast<const float*>(hmS + 8 * nc * nc);
-                for (int it = tid; it < nitem; it += NT_THREADS) {
-                    const int4 ix = aidx[it];
-                    const float2 c0 = cmul(hvS[ix.x & 0xFFFF], hmS[ix.y & 0xFFFF]);
-                    float2 c1 = cmul(hvS[ix.x >> 16], hmS[ix.y >> 16]);
-                    if (!(ix.w >> 8)) c1 = make_float2(0.f, 0.f);
-                    const float mh = -hcS[ix.w & 0xFF];
-                    const int o0 = ix.z & 0xFFFF, o1 = (ix.z >> 16) & 0xFFFF;
-                    *reinterpret_cast<uint4*>(A2 + o0) = pack_tf32(c0.x, -c0.y, c1.x, -c1.y);
-                    *reinterpret_cast<uint4*>(A2 + o1) = pack_tf32(c0.y, c0.x, c1.y, c1.x);
-                    *reinterpret_cast<uint4*>(A2 + A_KB + o0) = pack_tf32(mh * c0.x, -mh * c0.y, mh * c1.x, -mh * c1.y);
-                    *reinterpret_cast<uint4*>(A2 + A_KB + o1) = pack_tf32(mh * c0.y, mh * c0.x, mh * c1.y, mh * c1.x);
+                        for (int kk = 0; kk < NT_KB / 8; ++kk)
+                            mma(tD1, desc_sw128(sa + kk * 32), desc_sw128(sb + kk * 32), id1, (kb > 0 || kk > 0) ? 1u : 0u);
+                        commit(su32(&bar_empty[q]));
+                        if (i > 0) issue_s2(n2mma * (kb + 1) / (nkb + 1), false);
+                    }
+                    if (i > 0) issue_s2(n2mma, true);
+                    if (ok && i < nsl) commit(su32(&bar_d1_full));   // S1(i) and S2(i - 1) done: D1 full, B and Ahat free
                 }
+                __syncwarp();
+                ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             }
-            if (tid == 0 && !bar_wait(su32(&bar_d1), (uint32_t)(i & 1), status)) abort_flag = 1;
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncthreads();
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            if (abort_flag) break;
-            if (warp < 4) {
-                const int L = warp * 32 + lane, yz = L >> 6, j = L & 63;
+            if (i == nsl) break;
+            // convert D1(i) into B; the four warps meet at a named barrier every slot
+            bool got = ok && bar_spin(su32(&bar_d1_full), (uint32_t)(i & 1), status, abort_flag);
+            got = __all_sync(0xffffffffu, got);
+            if (got) {
+                tc_fence_after();
                 for (int ch = 0; ch < nch; ++ch) {
                     float v[32];
-                    tmem_ld32(tD1 + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ch * 32), v);
-                    unsigned char* dst = B2 + yz * (N2 * 128);
+                    tmem_ld32(tD1 + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ch * 32), v);
 #pragma unroll
                     for (int c = 0; c < 8; ++c)
                         *reinterpret_cast<uint4*>(dst + sw128(ch * 64 + j, 4 * c, N2)) =
                             pack_tf32(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
                 }
+                fence_async_smem();
             }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncthreads();
-            if (tid == 0) {
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t a0 = su32(A2), b0 = su32(B2);
+            ok = ok && got;
+            tc_fence_before();
+            converters_sync();                                   // D1 read, B(i) written
+            tc_fence_after();
+        }
+        if (warp == W_C0 && lane == 0) {
+            commit(su32(&bar_d2));
+            bar_drain(su32(&bar_d2), 0, status);                 // every MMA finished (also on the abort path)
+        }
+        __syncwarp();
+    } else if (warp >= W_P0 && warp < W_A1) {
+        // -------------------------------------------------- stage-1 producers
+        // Lane (row rr, float octet): each warp instruction copies 8 floats of
+        // 4 source rows; the octet is rotated by the row so that the 4 rows read
+        // different 32-byte chunks (distinct L1 banks), and the shared-memory
+        // destinations of the 32 lanes fall in 32 distinct banks.  Each warp
+        // keeps up to NT_STAGES K-blocks in flight: after issuing K-block kg it
+        // waits for its own copies of K-block kg - (NT_STAGES - 1) and signals
+        // that stage with one arrival per warp.
+        const int p = warp - W_P0;
+        const int rr = p * 4 + (lane & 3), n0 = lane >> 2, twot = 2 * t;
+        const size_t chs = (size_t)nk * 8 * t * 2;             // floats per chain of X
+        bool ok = true;
+        int issued = 0;
+        for (int kg = 0; kg < nkg; ++kg) {
+            const int q = kg % NT_STAGES;
+            if (kg >= NT_STAGES) ok = bar_wait(su32(&bar_empty[q]), (uint32_t)(((kg / NT_STAGES) - 1) & 1), status, abort_flag);
+            if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
+            const int i = s_ki[kg] & 0xFFFF, kb = s_ki[kg] >> 16;
+            const int4 si = s_sl[i];
+            const int r = kb * NT_KB + rr;
+            const int code = r < si.w ? (int)s_rows[s_rs[i] + r] : -1;
+            unsigned char* Sq = ring + q * lay.stage_bytes;
+            unsigned char* Bq = Sq + S_BYTES;
+            if (p == 0 && lane == 0) {
+                const uint32_t sb = su32(&bar_sfull[q]);
+                bar_arrive_tx(sb, S_BYTES);
+                bulk_copy(su32(Sq), Simg + (size_t)(si.y + kb) * S_BYTES, S_BYTES, sb);
+            }
+            if (code >= 0) {
+                const int js = code & 0xFF, l = code >> 8;
+                const float* src = X + (((size_t)scell[si.x * 8 + l] * Ndiv + js) * 8 + l) * t * 2;
+                for (int ch = 0; ch < nch; ++ch)
 #pragma unroll
-                for (int mh = 0; mh < 2; ++mh)
-#pragma unroll
-                    for (int kb2 = 0; kb2 < 2; ++kb2)
-#pragma unroll
-                        for (int kk = 0; kk < 4; ++kk)
-                            mma(tmem + (uint32_t)(mh * N2), desc_sw128(a0 + kb2 * A_KB + mh * (A_KB / 2) + kk * 32),
-                                desc_sw128(b0 + kb2 * N2 * 128 + kk * 32), id2, (i > 0 || kb2 > 0 || kk > 0) ? 1u : 0u);
-                commit(su32(&bar_mma2));
+                    for (int fo = 0; fo < 4; ++fo) {
+                        const int nn = (((fo + lane) & 3) << 3) + n0;
+                        if (nn < twot) cp_async4(Bq + sw128(ch * 32 + nn, rr, N1), src + ch * chs + nn);
+                    }
+            }
+            cp_async_commit();
+            ++issued;
+            if (kg >= NT_STAGES - 1) {
+                cp_async_wait_lag();                             // this thread's copies of K-block kg - (NT_STAGES - 1) landed
+                fence_async_smem();
+                __syncwarp();
+                if (lane == 0) bar_arrive(su32(&bar_full[(kg - (NT_STAGES - 1)) % NT_STAGES]));
             }
         }
+        cp_async_wait0();
+        fence_async_smem();
+        __syncwarp();
+        if (ok && lane == 0)                                     // the last NT_STAGES - 1 K-blocks
+            for (int j = std::max(0, issued - (NT_STAGES - 1)); j < issued; ++j) bar_arrive(su32(&bar_full[j % NT_STAGES]));
+        if (p == 0 && lane == 0)                                 // bulk copies in flight must land before exit
+            for (int j = std::max(0, issued - NT_STAGES); j < issued; ++j)
+                bar_drain(su32(&bar_sfull[j % NT_STAGES]), (uint32_t)((j / NT_STAGES) & 1), status);
+    } else {
+        // ------------------------------------------------------ Ahat writers
+        // Items (l, e, pair of e') are fixed per thread: decode them once.  The
+        // slot's head factors are staged one slot ahead by cp.async into
+        // hbuf[slot parity]; the writers never leave the loop early (named
+        // barriers), they skip the work once a wait gave up.
+        const int ta = (warp < W_C0 ? warp : warp - W_A1 + W_C0) * 32 + lane;
+        const int nvv = nv * nv, ncc = nc * nc, nitem = 8 * t * th, per = nvv + ncc + 1;
+        int d0[NT_AMAX], d1[NT_AMAX], d2[NT_AMAX];
+#pragma unroll
+        for (int k = 0; k < NT_AMAX; ++k) {
+            const int it = ta + k * NT_A;
+            d0[k] = d1[k] = d2[k] = -1;
+            if (it < nitem) {
+                const int l = it / (t * th), e = (it / th) % t, qp = it % th;
+                const int n1 = e / nc, n2 = e % nc, ep0 = 2 * qp, ep1 = 2 * qp + 1, has1 = ep1 < t;
+                const int e1 = has1 ? ep1 : ep0;
+                const int hv0 = l * nvv + n1 * nv + ep0 / nc, hv1 = l * nvv + n1 * nv + e1 / nc;
+                const int hm0 = l * ncc + n2 * nc + ep0 % nc, hm1 = l * ncc + n2 * nc + e1 % nc;
+                const int row = (l * t + e) * 2;
+                d0[k] = hv0 | (hv1 << 9) | (hm0 << 18);
+                d1[k] = hm1 | (((int)sw128(row, 4 * qp, NT_M) >> 4) << 9) | (l << 21) | (has1 << 24) | (((l * t + e) >= 64) << 25);
+                d2[k] = (int)sw128(row + 1, 4 * qp, NT_M) >> 4;
+            }
+        }
+        auto prefetch = [&](int i) {
+            const Int3 so = unflat3(s_sl[i].x, ns1);
+            const int oa = so.a + smin - rmin, ob = so.b + smin - rmin, oc = so.c + smin - rmin;
+            float2* hvS = reinterpret_cast<float2*>(hbuf + (i & 1) * hbb);
+            float2* hmS = hvS + 8 * nvv;
+            float* hcS = reinterpret_cast<float*>(hmS + 8 * ncc);
+            for (int j = ta; j < 8 * per; j += NT_A) {
+                const int l = j / per, w = j - l * per;
+                const int l1 = (l >> 2) & 1, l2 = (l >> 1) & 1, l3 = l & 1;
+                const int kt = flat3(ci.a + l1, ci.b + l2, ci.c + l3, n);
+                const int r = ((oa - l1) * nr1 + (ob - l2)) * nr1 + (oc - l3);
+                if (w < nvv) cp_async8(hvS + l * nvv + w, Hv + ((size_t)kt * nrel + r) * nvv + w);
+                else if (w < nvv + ncc) cp_async8(hmS + l * ncc + (w - nvv), Hc + ((size_t)kt * nrel + r) * ncc + (w - nvv));
+                else cp_async4(hcS + l, hc + r);
+            }
+        };
+        bool ok = true;
+        prefetch(0);
+        cp_async_commit();
+        for (int i = 0; i < nsl; ++i) {
+            writers_sync();                                      // every writer is done with slot i - 1's buffer
+            if (i + 1 < nsl) prefetch(i + 1);
+            cp_async_commit();
+            cp_async_wait1();                                    // this thread's copies for slot i landed
+            writers_sync();                                      // everyone's copies for slot i landed
+            const float2* hvS = reinterpret_cast<const float2*>(hbuf + (i & 1) * hbb);
+            const float2* hmS = hvS + 8 * nvv;
+            const float* hcS = reinterpret_cast<const float*>(hmS + 8 * ncc);
+            for (int mh = 0; mh < nmh; ++mh) {
+                if (ok && i > 0) ok = bar_wait(su32(&bar_a_free[mh]), (uint32_t)((i - 1) & 1), status, abort_flag);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) continue;
+#pragma unroll
+                for (int k = 0; k < NT_AMAX; ++k) {
+                    if (d0[k] < 0 || ((d1[k] >> 25) & 1) != mh) continue;
+                    const int l = (d1[k] >> 21) & 7;
+                    const float2 c0 = cmul(hvS[d0[k] & 511], hmS[(d0[k] >> 18) & 511]);
+                    const float2 c1 = ((d1[k] >> 24) & 1) ? cmul(hvS[(d0[k] >> 9) & 511], hmS[d1[k] & 511])
+                                                          : make_float2(0.f, 0.f);
+                    const float mhc = -hcS[l];
+                    const uint32_t o0 = (uint32_t)(((d1[k] >> 9) & 4095) << 4), o1 = (uint32_t)(d2[k] << 4);
+                    *reinterpret_cast<uint4*>(A2 + o0) = pack_tf32(c0.x, -c0.y, c1.x, -c1.y);
+                    *reinterpret_cast<uint4*>(A2 + o1) = pack_tf32(c0.y, c0.x, c1.y, c1.x);
+                    *reinterpret_cast<uint4*>(A2 + A_KB + o0) = pack_tf32(mhc * c0.x, -mhc * c0.y, mhc * c1.x, -mhc * c1.y);
+                    *reinterpret_cast<uint4*>(A2 + A_KB + o1) = pack_tf32(mhc * c0.y, mhc * c0.x, mhc * c1.y, mhc * c1.x);
+                }
+                fence_async_smem();
+                __syncwarp();
+                if (lane == 0) bar_arrive(su32(&bar_a_full[mh]));
+            }
+        }
+        cp_async_wait0();
     }
-    cp_async_wait0();
-    // all MMAs done before reading TMEM (and before freeing it on any path)
-    if (tid == 0) {
-        commit(su32(&bar_drain));
-        if (!bar_wait(su32(&bar_drain), 0, status)) abort_flag = 1;
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (!abort_flag) {
-        // epilogue: warp w reads TMEM lanes 32 (w % 4).. of items (half, 32-column chunk) w / 4, w / 4 + 4, ...
+
+    // ------------------------------------------------------------- epilogue
+    const bool done = bar_wait(su32(&bar_d2), 0, status, abort_flag);
+    if (__all_sync(0xffffffffu, done) && !*abort_flag) {
+        tc_fence_after();
+        // warp w reads TMEM lanes 32 (w % 4).. of items (half, 32-column chunk) w / 4, w / 4 + 6, ...
         const int quarter = warp & 3, cg = warp >> 2, nchunk = N2 / 32;
-        for (int item = cg; item < 2 * nchunk; item += 4) {
+        for (int item = cg; item < nmh * nchunk; item += NT_THREADS / 128) {
             const int mh = item / nchunk, c = item % nchunk, ch = c >> 1, j0 = (c & 1) * 32;
             float v[32];
             tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(mh * N2 + c * 32), v);
@@ -374,9 +534,12 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_near_tc(
             }
         }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    tc_fence_before();
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NT_TMEM_COLS));
+    if (warp == W_C0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NT_TMEM_COLS));
+    }
 }
 
 // S images: entry {K-block, target, row in K-block, near-offset index}; the
@@ -391,11 +554,10 @@ __global__ void k_near_pattern(const int4* __restrict__ ent, int nent, const flo
     *reinterpret_cast<uint32_t*>(b + sw128(64 + e.y, e.z, 128)) = f2tf32(1.0f);
 }
 
-size_t near_tc_smem(int nv, int nc, int nch, int nsl, int nkg, int nslot) {
-    const int t = nv * nc, th = (t + 1) / 2;
-    return 1024 + A_BYTES + (size_t)2 * 64 * nch * 128 + (size_t)NT_STAGES * (S_BYTES + 32 * nch * 128) +
-           2 * (size_t)hb_bytes(nv, nc) + 16 * (size_t)(8 * t * th) + 20 * (size_t)nsl + 4 * (size_t)nkg +
-           32 * (size_t)nslot;
+size_t near_tc_smem(int nv, int nc, int nch, int nsl, int nkg, int nslot, int nrows) {
+    const NtLayout lay(nch);
+    return 1024 + (size_t)lay.tab_off + 2 * (size_t)hb_bytes(nv, nc) + 20 * (size_t)nsl + 4 * (size_t)nkg +
+           32 * (size_t)nslot + 2 * (size_t)nrows;
 }
 
 }  // namespace
@@ -433,7 +595,7 @@ int bse_near_tc_prepare(bse_ctx* ctx, bse_interp* s, const std::vector<std::vect
     if (slots.empty() || slots.size() >= 65536) return BSE_OK;
     int maxsm = 0;
     cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
-    const size_t smem = near_tc_smem(s->nv, s->nc, 3, (int)slots.size(), (int)kinfo.size(), nslot);
+    const size_t smem = near_tc_smem(s->nv, s->nc, 3, (int)slots.size(), (int)kinfo.size(), nslot, (int)rows.size());
     if (smem > (size_t)maxsm) return BSE_OK;
     auto upload = [&](void** dst, const void* src, size_t bytes, const char* what) -> int {
         int rc = bse_alloc(ctx, dst, bytes, what);
@@ -461,6 +623,7 @@ int bse_near_tc_prepare(bse_ctx* ctx, bse_interp* s, const std::vector<std::vect
     }
     s->nf_tc_nsl = (int)slots.size();
     s->nf_tc_nkg = (int)kinfo.size();
+    s->nf_tc_nrows = (int)rows.size();
     s->nf_tc = 1;
     return BSE_OK;
 }
@@ -469,7 +632,7 @@ int bse_near_tc_launch(bse_ctx* ctx, const bse_interp* s, int nchains, const voi
     // at most three chains per launch (TMEM: 160 columns per chain)
     for (int c0 = 0; c0 < nchains; c0 += 3) {
         const int nch = std::min(3, nchains - c0);
-        const size_t smem = near_tc_smem(s->nv, s->nc, nch, s->nf_tc_nsl, s->nf_tc_nkg, s->nslot);
+        const size_t smem = near_tc_smem(s->nv, s->nc, nch, s->nf_tc_nsl, s->nf_tc_nkg, s->nslot, s->nf_tc_nrows);
         // handles of different sizes share the kernel's attribute: only ever raise it
         cudaFuncAttributes fa;
         BSE_CUDA_TRY(ctx, cudaFuncGetAttributes(&fa, k_near_tc));
@@ -478,7 +641,7 @@ int bse_near_tc_launch(bse_ctx* ctx, const bse_interp* s, int nchains, const voi
         const size_t off = (size_t)c0 * s->nk * 8 * s->t;
         k_near_tc<<<s->co->nkc, NT_THREADS, smem, ctx->stream>>>(
             (const float*)((const float2*)X + off), s->d_tc_rows, s->d_tc_slots, s->d_tc_rowstart, s->d_tc_kinfo,
-            s->nf_tc_nsl, s->nf_tc_nkg, s->d_tc_simg, (const float2*)s->d_Hv, (const float2*)s->d_Hc,
+            s->nf_tc_nsl, s->nf_tc_nkg, s->nf_tc_nrows, s->d_tc_simg, (const float2*)s->d_Hv, (const float2*)s->d_Hc,
             (const float*)s->d_hc, s->n, s->nd, s->nv, s->nc, s->nb1, s->smin, s->ns1, s->rmin, s->nr1, nch,
             (float2*)U + off, ctx->d_status);
     }

@@ -109,7 +109,7 @@ extern "C" int bse_apply_h_noalloc(bse_ctx* ctx, bse_interp* s, int nvec, const 
     BSE_CUDA_TRY(ctx, cudaMemcpy(&status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
     if (status) {
         cudaMemset(ctx->d_status, 0, sizeof(int));
-        ctx->err = "a bounded device wait in the tensor-core K_c apply gave up";
+        ctx->err = bse_timeout_message(status);
         return BSE_ERR_TIMEOUT;
     }
     return BSE_OK;
