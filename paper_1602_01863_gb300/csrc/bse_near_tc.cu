@@ -27,7 +27,8 @@
 //   warps 4-7      MMA issuer (warp 4, lane 0, also TMEM owner) and D1 -> B
 //                  converters (TMEM lane quarters 0-3); after each slot the four
 //                  warps convert D1 and meet at a named barrier, after which the
-//                  issuer goes on, so this hand-off never sleeps on an mbarrier
+//                  issuer goes on.  Waits use the blocking mbarrier test: a
+//                  spinning issuer measurably slowed the other warps
 //   warps 8-15     stage-1 producers: the S image by one bulk copy, the X rows by
 //                  4-byte cp.async gathers laid out so that a warp's 32 stores
 //                  hit 32 distinct banks; each warp keeps the whole ring in
@@ -130,24 +131,6 @@ __device__ __forceinline__ bool bar_wait(uint32_t b, uint32_t parity, int* statu
         }
     }
     return true;
-}
-// Bounded spin on the non-blocking test, for the roles on the critical path
-// (MMA issuer, converters): no suspension, so no wake-up latency.
-__device__ __forceinline__ bool bar_spin(uint32_t b, uint32_t parity, int* status, volatile int* abort_flag) {
-    long long t0 = -1;
-    for (int it = 1;; ++it) {
-        if (bar_test(b, parity)) return true;
-        if ((it & 63) == 0) {
-            if (*abort_flag) return false;
-            const long long now = clock64();
-            if (t0 < 0) t0 = now;
-            else if (now - t0 > NT_WAIT_CYCLES) {
-                atomicOr(status, 2);
-                *abort_flag = 1;
-                return false;
-            }
-        }
-    }
 }
 // Wait that ignores the abort flag (drain paths: copies and MMAs in flight always finish).
 __device__ __forceinline__ void bar_drain(uint32_t b, uint32_t parity, int* status) {
@@ -312,15 +295,14 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_near_tc(
                     // phase i: stage 1 of slot i (i < nsl) with stage 2 of slot i - 1 (i > 0) spread between its K-blocks
                     const int nkb = (i < nsl) ? s_sl[i].z : 0;
                     int s2 = 0;                                  // next stage-2 MMA
-                    // stage-2 MMAs up to `upto`; between K-blocks (force = false) a half
-                    // whose Ahat is not ready yet is left for later instead of waited for
+                    // stage-2 MMAs up to `upto` (waiting for a half's Ahat when it is not ready)
                     auto issue_s2 = [&](int upto, bool force) {
+                        (void)force;
                         while (ok && s2 < upto) {
                             const int mh = s2 >> 3, yzb = (s2 >> 2) & 1, kk = s2 & 3;
                             if ((s2 & 7) == 0) {
                                 const uint32_t ab = su32(&bar_a_full[mh]), par = (uint32_t)((i - 1) & 1);
-                                if (!force && !bar_test(ab, par)) return;
-                                ok = bar_spin(ab, par, status, abort_flag);
+                                ok = bar_wait(ab, par, status, abort_flag);
                                 if (!ok) return;
                                 tc_fence_after();
                             }
@@ -333,8 +315,8 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_near_tc(
                     for (int kb = 0; kb < nkb && ok; ++kb, ++kg) {
                         const int q = kg % NT_STAGES;
                         const uint32_t par = (uint32_t)((kg / NT_STAGES) & 1);
-                        ok = bar_spin(su32(&bar_full[q]), par, status, abort_flag) &&
-                             bar_spin(su32(&bar_sfull[q]), par, status, abort_flag);
+                        ok = bar_wait(su32(&bar_full[q]), par, status, abort_flag) &&
+                             bar_wait(su32(&bar_sfull[q]), par, status, abort_flag);
                         if (!ok) break;
                         fence_async_smem();                      // the producers' cp.async writes, for the async proxy
                         tc_fence_after();
@@ -353,7 +335,7 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_near_tc(
             }
             if (i == nsl) break;
             // convert D1(i) into B; the four warps meet at a named barrier every slot
-            bool got = ok && bar_spin(su32(&bar_d1_full), (uint32_t)(i & 1), status, abort_flag);
+            bool got = ok && bar_wait(su32(&bar_d1_full), (uint32_t)(i & 1), status, abort_flag);
             got = __all_sync(0xffffffffu, got);
             if (got) {
                 tc_fence_after();
