@@ -1312,7 +1312,7 @@ inline int dot_blocks(const bse_interp* s) {
     return vec_blocks(s->N);
 }
 
-// Restrict: register-blocked FP32 kernel for 3x3 and 4x4 bands, generic otherwise.
+// Restrict: staged FP32 kernel for 3x3, 4x4 and 4x6 bands (N_div <= 64), generic otherwise.
 template <typename T>
 void launch_restrict(bse_ctx* ctx, const bse_interp* s, int nchains, const void* psi, void* Q, __nv_bfloat16* bop,
                      void* X) {
@@ -1354,7 +1354,7 @@ void launch_restrict(bse_ctx* ctx, const bse_interp* s, int nchains, const void*
                                                     (V*)X, nullptr);
 }
 
-// Prolong + diagonal: register-blocked FP32 kernel for 3x3, 4x4, 4x6 bands, generic otherwise.
+// Prolong + diagonal: staged FP32 kernel for 3x3, 4x4 and 4x6 bands (N_div <= 64), generic otherwise.
 template <typename T>
 void launch_prolong(bse_ctx* ctx, const bse_interp* s, int nchains, const void* R, const void* U, const void* psi,
                     void* W, double2* dot) {

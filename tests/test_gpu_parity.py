@@ -109,7 +109,7 @@ def test_apply_h_f64_matches_oracle(ctx, case):
 
 @pytest.mark.parametrize("nv,nc,method", [(4, 4, "m3"), (4, 6, "m3"), (3, 3, "m3"), (2, 3, "m3"), (4, 4, "m1")])
 def test_apply_h_fp32_matches_oracle(ctx, nv, nc, method):
-    """FP32 vectors with complex64 K_c (register-blocked kernels for 3x3, 4x4
+    """FP32 vectors with complex64 K_c (staged kernels for 3x3, 4x4
     and 4x6 bands, generic ones otherwise, CUDA-core near field), 3 chains:
     FP32-level agreement."""
     from paper_1602_01863_gb300 import bse
