@@ -69,3 +69,30 @@ def test_model_struct_layout():
     s, keep = bse.model_struct(m)
     assert s.nv == 3 and s.nc == 2 and s.direct_shells == 27
     assert keep[3].size == 2 * 7 * 26 * 3 * 2 and keep[4].size == 2 * 7 * 3 * 3 * 2
+
+
+def test_null_arguments_are_rejected_on_the_host(built_lib):
+    """Corrupt arguments (NULL handles and outputs) come back as BSE_ERR_ARG
+    (-1) from every entry point before any device call, so these checks run
+    without a GPU."""
+    lib = built_lib
+    P, N = ctypes.c_void_p, None
+    dummy = (ctypes.c_double * 8)()
+    idummy = (ctypes.c_int * 8)()
+    lldummy = (ctypes.c_longlong * 8)()
+    calls = {
+        "bse_ctx_create": lambda: lib.bse_ctx_create(N, 0, N),
+        "bse_build_coarse": lambda: lib.bse_build_coarse(N, N, 4, 0, N),
+        "bse_coarse_get_kc": lambda: lib.bse_coarse_get_kc(N, N, dummy),
+        "bse_interp_setup": lambda: lib.bse_interp_setup(N, N, 2, 0, ctypes.c_double(1.0), 0, N),
+        "bse_interp_info": lambda: lib.bse_interp_info(N, lldummy),
+        "bse_dipoles": lambda: lib.bse_dipoles(N, N, 1, dummy, N, dummy),
+        "bse_apply_h": lambda: lib.bse_apply_h(N, N, 1, N, N),
+        "bse_apply_h_noalloc": lambda: lib.bse_apply_h_noalloc(N, N, 1, N, N),
+        "bse_haydock_run": lambda: lib.bse_haydock_run(N, N, 1, idummy, dummy, 4, 0, dummy, dummy, dummy, idummy),
+        "bse_last_kernel_times": lambda: lib.bse_last_kernel_times(N, dummy, lldummy),
+        "bse_spectrum": lambda: lib.bse_spectrum(N, 1, 4, idummy, dummy, dummy, dummy, ctypes.c_double(1.0),
+                                                 ctypes.c_double(0.1), 4, dummy, dummy),
+    }
+    for name, call in calls.items():
+        assert call() == -1, name
