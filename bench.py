@@ -184,7 +184,7 @@ def near_field_work(nd, width, t, nchains, nkc, nb1=False):
     nmh = 2 if 16 * t > 128 else 1
     issued = nkc * 2 * (nkg * 128 * 32 * nchains * 32 + len(rows) * nmh * 128 * 64 * nchains * 64)
     return {"useful_flops": float(useful), "issued_flops": float(issued), "near_pairs_per_cell": pairs,
-            "k_blocks_per_cell": nkg, "slots_per_cell": len(rows)}
+            "head_blocks_per_cell": s2, "k_blocks_per_cell": nkg, "slots_per_cell": len(rows)}
 
 
 def time_runs(ctx, bse, it, dirs, m, flags, steps, warmup, omega, pref, eta, barrier):
