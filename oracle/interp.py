@@ -10,6 +10,8 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
   M1         Eq. interp1 = F K_c F^H, with the 1/N_div weight change from a
              coarse to a dense BZ sum:  K^{M1} = (1/N_div) F K_c F^H.
   matmul1-3  The same product without the dense matrix (Eqs. matmul1-3).
+  M2         Sec. 4: every pair keeps the interpolated coefficients of Eq. diverg
+             and divides the head by the dense q (dense matrix, small systems only).
   M3         Sec. 4: pairs with ||k - k'|| <= w d keep the interpolated
              divergent coefficient a (Eq. diverg) and divide by the dense q:
              K^{M3} = (1/N_div)[ (F A F^H) h_head(q_dense) + F (K_c - A h_head(q_coarse)) F^H ].
@@ -103,8 +105,22 @@ class Interp:
         delta = np.where(near_blk, (FA * hd_blk - FAh) / self.Ndiv, 0.0)
         return self.K_m1_dense() + delta
 
+    def K_m2_dense(self) -> np.ndarray:
+        """K^{M2} (Sec. 4, "Method 2"): the coefficients of Eq. diverg are
+        interpolated for every dense pair and the divergent head is divided by
+        the dense q everywhere (no width):
+        (1/N_div)[(F A F^H) h_head(q_dense) + F (K_c - A h_head(q_coarse)) F^H].
+        The model has no 1/q wing (b = 0), so a and c are the only terms."""
+        F = self.F()
+        t = self.t
+        _, hd = self.dense_q_tables()
+        FA = F @ self.A @ F.conj().T
+        Hc_blk = np.kron(self.Hhead_c, np.ones((t, t)))
+        FC = F @ (self.Kc - self.A * Hc_blk) @ F.conj().T
+        return (FA * np.kron(hd, np.ones((t, t))) + FC) / self.Ndiv
+
     def H_dense(self, method: str = "m1") -> np.ndarray:
-        K = self.K_m1_dense() if method == "m1" else self.K_m3_dense()
+        K = {"m1": self.K_m1_dense, "m2": self.K_m2_dense, "m3": self.K_m3_dense}[method]()
         return np.diag(self.dE).astype(np.complex128) + K
 
     # ------------------------------------------------------- matrix-free form

@@ -350,3 +350,28 @@ def test_sampled_rows_match_matrix_free_apply():
     assert np.abs(I.apply_m1_rows(v, rows) - full).max() < 1e-13
     Kr = om.kernel_rows(I.coarse, np.array([1, 5]))
     assert np.abs(Kr - I.Kc[np.r_[I.t:2 * I.t, 5 * I.t:6 * I.t]]).max() < 1e-15
+
+
+# ------------------------------------------------------------------- Method 2
+def test_m2_exact_on_every_pair_for_head_only_model():
+    """Method 2 (Sec. 4) interpolates a and c for every pair and divides by the
+    dense q.  G = 0 shell only and constant mu: a and c are interpolated
+    exactly, so M2 equals the explicit kernel on every pair (near and far),
+    where M3 is exact only on near pairs; M2 = M3 on near pairs in general."""
+    I = tiny_interp(n=4, nd=2, nv=2, nc=2, const_mu=True, shells=1, width=1.0)
+    Hx, _ = om.explicit_dense_hamiltonian(I.model, 4, 2)
+    H2, H3 = I.H_dense("m2"), I.H_dense("m3")
+    assert np.abs(H2 - Hx).max() < 1e-13
+    near, _ = I.dense_q_tables()
+    nb = np.kron(near, np.ones((I.t, I.t))).astype(bool)
+    assert np.abs((H3 - Hx)[~nb]).max() > 1e-5                 # M3 is M1 (inexact) on far pairs
+    J = tiny_interp(n=4, nd=2, nv=2, nc=2, width=1.0)          # varying model
+    assert np.abs((J.H_dense("m2") - J.H_dense("m3"))[nb]).max() < 1e-15
+    assert np.abs(J.H_dense("m2") - J.H_dense("m2").conj().T).max() < 1e-15
+
+
+def test_m2_with_ndiv1_is_explicit():
+    """Dense mesh = coarse mesh: M2 reduces to the explicit kernel too."""
+    I = tiny_interp(n=3, nd=1, nv=2, nc=2, width=1.0)
+    Hx, _ = om.explicit_dense_hamiltonian(I.model, 3, 1)
+    assert np.abs(I.H_dense("m2") - Hx).max() < 1e-13
