@@ -64,9 +64,14 @@ extern "C" {
 
 /* ------------------------------------------------------------ Haydock flags */
 #define BSE_REORTH_CGS2   1  /* full reorthogonalisation, classical Gram-Schmidt x2 */
-#define BSE_USE_GRAPH     2  /* capture the step loop in a CUDA graph (cached)      */
+#define BSE_USE_GRAPH     2  /* run the step loop as a CUDA graph; the instantiated
+                                graph is kept in the handle (or, for a batch, in
+                                the context) and replayed by the next run with
+                                the same chains, steps and flags                    */
 #define BSE_PROFILE       4  /* time the kernel classes with events (see
                                 bse_last_kernel_times)                              */
+#define BSE_STOP_CONVERGED 8 /* stop each chain once its spectrum has converged by
+                                the rule set with bse_set_stop_rule (Sec. 5.1)      */
 
 /* Synthetic model crystal (stand-in for the ab initio inputs of Sec. 2,
  * Eqs. bse2-bse3b).  All arrays are host, row-major, complex interleaved:
@@ -122,13 +127,38 @@ const char* bse_last_error(const bse_ctx* ctx);
  * (BSE_PREC_F64 complex128, BSE_PREC_F32 complex64, BSE_PREC_BF16 planes),
  * and the head factors of Eq. diverg (the G = 0 direct term,
  * A_c = alpha O^v (x) O^c with alpha = -(e_k / n^3) 4 pi / eps_inf).
+ * `user_kc` (nullable) is a device complex128 [N_c][N_c] row-major K_c
+ * (Sec. 4: the coarse BSE matrix elements computed elsewhere, e.g. from ab
+ * initio wavefunctions) that replaces the model's kernel; it is read during
+ * the call only and converted to `kc_prec`.  The model still supplies the
+ * band gauge (overlaps d and the Method-3 head factors) and the sizes; with a
+ * user K_c, Method 3 takes c = K_c - A_c h_head(q_c) for the remainder.  A
+ * non-finite user K_c entry is stored as it is and propagates.
  * Errors: BSE_ERR_ARG (nv, nc outside 1..8, n < 1, non-finite model numbers,
  * direct_shells not 1 or 27), BSE_ERR_OOM, BSE_ERR_CUDA. */
 int bse_build_coarse(bse_ctx* ctx, const bse_model* model, int n_coarse, int kc_prec,
-                     bse_coarse** out);
+                     const void* user_kc, bse_coarse** out);
 /* Copy K_c to host as complex128 [N_c][N_c] (converted from its storage). */
 int bse_coarse_get_kc(bse_ctx* ctx, const bse_coarse* coarse, double* host_kc);
 void bse_free_coarse(bse_coarse* coarse);
+
+/* Dense-mesh inputs supplied by the caller instead of the model (all host,
+ * complex numbers interleaved, dense points in the coarse-major order above,
+ * N = t N_k):
+ *   dE  [N]                 real, Delta E_vck = e_ck - e_vk (Eq. bse1), eV
+ *   P   [3][N]              complex128, dipoles P^alpha_vck (Eq. epsmacro)
+ *   Dv  [N_k][8][nv][nv]    complex128, Dv[kd][l][n'][v] = d_{v k}^{n' k~_l}, the
+ *   Dc  [N_k][8][nc][nc]    overlaps of Eq. completeness with the 8 coarse corners
+ *                           k~_l = k~(i + (l1, l2, l3)), l = 4 l1 + 2 l2 + l3
+ *                           (corners of zero weight are not read)
+ * Any pointer may be NULL: that table then comes from the model.  Read during
+ * bse_interp_setup only.  Non-finite entries are rejected (BSE_ERR_ARG). */
+typedef struct bse_dense_inputs {
+    const double* dE;
+    const double* P;
+    const double* Dv;
+    const double* Dc;
+} bse_dense_inputs;
 
 /* Interpolation set-up for one dense mesh refining `coarse` by n_div per
  * axis (Sec. 3): dense Delta E (exact on the dense mesh), dipoles P^alpha,
@@ -146,10 +176,12 @@ void bse_free_coarse(bse_coarse* coarse);
  * With BF16 K_c the set-up autotunes the tensor-core apply: it times a few
  * splits of the K_c stream over the SMs on this K_c and keeps the fastest
  * (cached per shape for the process).
+ * `dense` (nullable) replaces the model's dense tables (bse_dense_inputs).
  * Errors: BSE_ERR_ARG (n_div < 1; M3 with width_w >= n / 2, where the near
- * region would wrap around the zone; bad flags), BSE_ERR_OOM, BSE_ERR_CUDA. */
+ * region would wrap around the zone; bad flags; non-finite dense inputs),
+ * BSE_ERR_OOM, BSE_ERR_CUDA. */
 int bse_interp_setup(bse_ctx* ctx, const bse_coarse* coarse, int n_div, int scheme,
-                     double width_w, int vec_prec, bse_interp** out);
+                     double width_w, int vec_prec, const bse_dense_inputs* dense, bse_interp** out);
 void bse_free_interp(bse_interp* interp);
 
 /* Sizes of an interp handle: info[0] = N (dense dimension), [1] = N_k,
@@ -172,20 +204,41 @@ int bse_apply_h(bse_ctx* ctx, bse_interp* interp, int nvec, const void* x, void*
 
 /* Same result as bse_apply_h, but allocates no device memory: the per-call
  * scratch comes from one static device array of 32 MiB inside the library
- * (held by every GPU that loads the library until the process exits), not
- * from the handle.  The paper has no counterpart; this exists for callers
- * that must not call cudaMalloc once their work has started, such as a host
- * framework that owns all device memory through its own pool, or a loop
- * where cudaMalloc's implicit device synchronisation is not allowed.
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  All calls share the array and it keeps the
+ * (held by a device from the time the library's device module is loaded on
+ * it, at the latest the first bse_ctx_create on that device, until the
+ * process exits), not from the handle.  The paper has no counterpart; this
+ * exists for callers that must not call cudaMalloc once their work has
+ * started, such as a host framework that owns all device memory through its
+ * own pool, or a loop where cudaMalloc's implicit device synchronisation is
+ * not allowed.  bse_ctx_create looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current), which also loads the
+ * module under lazy loading; create the context before any stream capture.
+ * All calls share the array and it keeps the
  * previous call's contents (what must start at zero is cleared each call):
  * calls that overlap on the GPU race.  Sizes whose scratch does not fit
  * (nvec vectors of Q and R, for M3 the per-corner pieces, for BF16 the
  * operand and tile partials) return BSE_ERR_UNSUPPORTED with the byte count
  * in bse_last_error.  Other errors as bse_apply_h. */
 int bse_apply_h_noalloc(bse_ctx* ctx, bse_interp* interp, int nvec, const void* x, void* y);
+
+/* Stopping rule for BSE_STOP_CONVERGED runs (Sec. 5.1: the chains were
+ * stopped once the whole dielectric spectrum changed by less than 1 % in its
+ * real and in its imaginary part).  Every `check_every` steps each chain
+ * evaluates eps(omega) on the device (Eq. fraccont, FP64, the steps done so
+ * far) with eps = 1 - (s_eps / N_k) ||P||^2 g_1(omega + i eta) on the `nw`
+ * frequencies `omega` (host, copied), and stops at the first check where
+ *   max_w |Re eps - Re eps_prev| <= tol max_w |Re eps|   and
+ *   max_w |Im eps - Im eps_prev| <= tol max_w |Im eps|,
+ * eps_prev being the previous check's spectrum (so no chain stops before
+ * 2 check_every steps).  steps_done then reports the steps run.  Such a chain
+ * is not a breakdown: it does not raise BSE_WARN_BREAKDOWN.  A single system
+ * run with this flag is issued check by check and ends as soon as every chain
+ * has stopped (BSE_USE_GRAPH is then not used); in a batch the stopped chains
+ * skip their work inside the one graph.  The rule stays set on the context.
+ * Errors: BSE_ERR_ARG (tol <= 0, check_every < 1, eta <= 0, nw < 1,
+ * non-finite numbers), BSE_ERR_OOM, BSE_ERR_CUDA. */
+int bse_set_stop_rule(bse_ctx* ctx, double tol, int check_every, double s_eps, double eta, int nw,
+                      const double* omega);
 
 /* Haydock recursion (Eqs. ai, bi, ci) for `nsys` systems sharing the context.
  * System s runs npol[s] (1..4) chains starting from P(e) for the directions
@@ -199,9 +252,11 @@ int bse_apply_h_noalloc(bse_ctx* ctx, bse_interp* interp, int nvec, const void* 
  * graph (each system's loop on its own branch, longest systems spread over up
  * to 8 concurrent branches) and launched once; the results equal the
  * systems run one by one.  Each handle may appear once (it owns the scratch).
- * flags: BSE_REORTH_CGS2, BSE_USE_GRAPH, BSE_PROFILE.  A chain whose
- * b_{i+1} < 1e-12 max|a| stops there (BSE_WARN_BREAKDOWN).  Device waits
- * are bounded; a wait that gives up returns BSE_ERR_TIMEOUT. */
+ * flags: BSE_REORTH_CGS2, BSE_USE_GRAPH, BSE_PROFILE, BSE_STOP_CONVERGED.  A
+ * chain whose b_{i+1} < 1e-12 max|a| stops there (BSE_WARN_BREAKDOWN).
+ * Device waits are bounded; a wait that gives up returns BSE_ERR_TIMEOUT.
+ * No device memory is allocated after the first run of a handle with a given
+ * number of steps (the per-run buffers live in the handle). */
 int bse_haydock_run(bse_ctx* ctx, bse_interp* const* sys, int nsys, const int* npol,
                     const double* pol_dirs, int nsteps, int flags, double* a, double* b,
                     double* pnorm2, int* steps_done);

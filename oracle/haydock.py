@@ -10,7 +10,7 @@ from __future__ import annotations
 import numpy as np
 
 
-def haydock(apply_h, p: np.ndarray, m: int, reorth: str = "none", breakdown_tol: float = 1e-12):
+def haydock(apply_h, p: np.ndarray, m: int, reorth: str = "none", breakdown_tol: float = 1e-12, stop=None):
     """Eqs. ai, bi, ci.
 
       b_1 = 0, psi_1 = P / ||P||
@@ -19,7 +19,9 @@ def haydock(apply_h, p: np.ndarray, m: int, reorth: str = "none", breakdown_tol:
       [reorth = "cgs2": classical Gram-Schmidt of w against psi_1..psi_i, twice]
       b_{i+1} = ||w||,  psi_{i+1} = w / b_{i+1}
 
-    Stops early when b_{i+1} < breakdown_tol * max_j |a_j| (invariant subspace).
+    Stops early when b_{i+1} < breakdown_tol * max_j |a_j| (invariant subspace),
+    or when stop(a, b, ||P||^2) returns True after a step (the coefficients of
+    the steps done so far).
     Returns (a [steps], b [steps + 1], ||P||^2, imag_a [steps]).
     """
     pn2 = float(np.vdot(p, p).real)
@@ -42,6 +44,8 @@ def haydock(apply_h, p: np.ndarray, m: int, reorth: str = "none", breakdown_tol:
         bn = float(np.sqrt(np.vdot(w, w).real))
         b.append(bn)
         if bn < breakdown_tol * max(abs(x) for x in a):
+            break
+        if stop is not None and stop(np.array(a), np.array(b), pn2):
             break
         psi_prev, psi = psi, w / bn
         basis.append(psi)
@@ -91,3 +95,36 @@ def gauss_nodes(a, b, pn2):
 def spectrum_error(eps_im: np.ndarray, ref_im: np.ndarray) -> float:
     """max_w |Im eps - Im eps_ref| / max_w |Im eps_ref| (peak-normalised)."""
     return float(np.max(np.abs(eps_im - ref_im)) / np.max(np.abs(ref_im)))
+
+
+def spectrum_change(eps_new: np.ndarray, eps_old: np.ndarray) -> tuple[float, float]:
+    """Largest change of the real and of the imaginary part of eps over the
+    frequency window, each relative to the largest |part| of the new spectrum."""
+    d_re = float(np.max(np.abs(eps_new.real - eps_old.real)) / np.max(np.abs(eps_new.real)))
+    d_im = float(np.max(np.abs(eps_new.imag - eps_old.imag)) / np.max(np.abs(eps_new.imag)))
+    return d_re, d_im
+
+
+def haydock_until_converged(apply_h, p: np.ndarray, max_steps: int, check_every: int, tol: float, prefactor,
+                            eta, omega, reorth: str = "none"):
+    """The stopping rule of Sec. 5.1: the chain runs until the whole dielectric
+    spectrum changes by less than `tol` (1 %) in both its real and imaginary
+    part.  Reading: eps is evaluated (Eq. fraccont) after every `check_every`
+    steps, compared with the previous evaluation by spectrum_change, and the
+    chain stops at the first check where both changes are <= tol.
+    Returns haydock()'s tuple; len(a) is the number of steps done."""
+    prev = {}
+
+    def stop(a, b, pn2):
+        j = len(a)
+        if j % check_every:
+            return False
+        eps = epsilon(a, b, pn2, prefactor, eta, omega)
+        old = prev.get("eps")
+        prev["eps"] = eps
+        if old is None:
+            return False
+        d_re, d_im = spectrum_change(eps, old)
+        return d_re <= tol and d_im <= tol
+
+    return haydock(apply_h, p, max_steps, reorth, stop=stop)

@@ -27,7 +27,7 @@ BSE_WARN_BREAKDOWN = 1
 
 PREC_F64, PREC_F32, PREC_BF16 = 0, 1, 2
 SCHEME_M1, SCHEME_M3, NB1, NF_CUDA_CORES = 0, 1, 16, 32
-REORTH_CGS2, USE_GRAPH, PROFILE = 1, 2, 4
+REORTH_CGS2, USE_GRAPH, PROFILE, STOP_CONVERGED = 1, 2, 4, 8
 
 KERNEL_CLASSES = ("restrict", "kc_apply", "prolong", "near_field", "lanczos")
 
@@ -36,7 +36,7 @@ EXPORTED = ("bse_version", "bse_ctx_create", "bse_ctx_destroy", "bse_last_error"
             "bse_dipoles", "bse_apply_h", "bse_apply_h_noalloc", "bse_haydock_run", "bse_last_kernel_times",
             "bse_spectrum", "bse_mlp_param_count", "bse_mlp_create", "bse_mlp_free", "bse_mlp_get_params",
             "bse_mlp_forward", "bse_mlp_gradients", "bse_mlp_train_step", "bse_pairs_generate",
-            "bse_interp_set_learned")
+            "bse_interp_set_learned", "bse_set_stop_rule")
 
 
 class BseError(RuntimeError):
@@ -54,6 +54,11 @@ class bse_model(C.Structure):
                 ("offsets", C.POINTER(C.c_double)), ("gen_v", C.POINTER(C.c_double)),
                 ("gen_c", C.POINTER(C.c_double)), ("mu", C.POINTER(C.c_double)),
                 ("dip", C.POINTER(C.c_double))]
+
+
+class bse_dense_inputs(C.Structure):
+    _fields_ = [("dE", C.POINTER(C.c_double)), ("P", C.POINTER(C.c_double)),
+                ("Dv", C.POINTER(C.c_double)), ("Dc", C.POINTER(C.c_double))]
 
 
 _lib = None
@@ -77,11 +82,13 @@ def load(path: str | None = None):
     lib.bse_ctx_destroy.restype = None
     lib.bse_last_error.argtypes = [_P]
     lib.bse_last_error.restype = C.c_char_p
-    lib.bse_build_coarse.argtypes = [_P, C.POINTER(bse_model), C.c_int, C.c_int, C.POINTER(_P)]
+    lib.bse_build_coarse.argtypes = [_P, C.POINTER(bse_model), C.c_int, C.c_int, _P, C.POINTER(_P)]
     lib.bse_coarse_get_kc.argtypes = [_P, _P, _D]
     lib.bse_free_coarse.argtypes = [_P]
     lib.bse_free_coarse.restype = None
-    lib.bse_interp_setup.argtypes = [_P, _P, C.c_int, C.c_int, C.c_double, C.c_int, C.POINTER(_P)]
+    lib.bse_interp_setup.argtypes = [_P, _P, C.c_int, C.c_int, C.c_double, C.c_int, C.POINTER(bse_dense_inputs),
+                                     C.POINTER(_P)]
+    lib.bse_set_stop_rule.argtypes = [_P, C.c_double, C.c_int, C.c_double, C.c_double, C.c_int, _D]
     lib.bse_free_interp.argtypes = [_P]
     lib.bse_free_interp.restype = None
     lib.bse_interp_info.argtypes = [_P, C.POINTER(C.c_longlong)]
@@ -214,19 +221,41 @@ class Context:
             self.h = None
 
     # -- bse_build_coarse
-    def bse_build_coarse(self, model: ModelParams, n_coarse: int, kc_prec: int = PREC_F64) -> Coarse:
+    def bse_build_coarse(self, model: ModelParams, n_coarse: int, kc_prec: int = PREC_F64,
+                         user_kc_ptr: int = 0) -> Coarse:
+        """user_kc_ptr: device address of a complex128 [N_c, N_c] K_c replacing the model's (0: none)."""
         s, keep = model_struct(model)
         h = _P()
-        self._check(self.lib.bse_build_coarse(self.h, C.byref(s), n_coarse, kc_prec, C.byref(h)))
+        self._check(self.lib.bse_build_coarse(self.h, C.byref(s), n_coarse, kc_prec,
+                                              _P(user_kc_ptr) if user_kc_ptr else None, C.byref(h)))
         del keep
         return Coarse(self, h, n_coarse, model.nv * model.nc, kc_prec)
 
     # -- bse_interp_setup
     def bse_interp_setup(self, coarse: Coarse, n_div: int, scheme: int = SCHEME_M1, width: float = 1.0,
-                         vec_prec: int = PREC_F64) -> Interp:
+                         vec_prec: int = PREC_F64, dense: dict | None = None) -> Interp:
+        """dense: optional host arrays replacing the model's dense tables, keys
+        'dE' (float64 [N]), 'P' (complex128 [3, N]), 'Dv' (complex128 [N_k, 8, nv, nv]),
+        'Dc' (complex128 [N_k, 8, nc, nc])."""
         h = _P()
-        self._check(self.lib.bse_interp_setup(self.h, coarse.handle, n_div, scheme, float(width), vec_prec, C.byref(h)))
+        keep, din = [], None
+        if dense:
+            din = bse_dense_inputs()
+            for key, dt in (("dE", np.float64), ("P", np.complex128), ("Dv", np.complex128), ("Dc", np.complex128)):
+                if dense.get(key) is not None:
+                    arr = np.ascontiguousarray(dense[key], dtype=dt)
+                    keep.append(arr)
+                    setattr(din, key, arr.view(np.float64).ctypes.data_as(_D))
+        self._check(self.lib.bse_interp_setup(self.h, coarse.handle, n_div, scheme, float(width), vec_prec,
+                                              C.byref(din) if din is not None else None, C.byref(h)))
+        del keep
         return Interp(self, h, coarse)
+
+    # -- bse_set_stop_rule
+    def bse_set_stop_rule(self, tol: float, check_every: int, s_eps: float, eta: float, omega: np.ndarray) -> None:
+        w = np.ascontiguousarray(omega, dtype=np.float64)
+        self._check(self.lib.bse_set_stop_rule(self.h, float(tol), int(check_every), float(s_eps), float(eta),
+                                               w.size, _dptr(w)))
 
     # -- bse_dipoles
     def bse_dipoles(self, interp: Interp, pol_dirs: np.ndarray, out_ptr: int) -> np.ndarray:

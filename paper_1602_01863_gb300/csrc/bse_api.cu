@@ -1,6 +1,7 @@
 // extern "C" entry points of the library (see include/bse.h for the contract).
 #include <cmath>
 #include <cstring>
+#include <atomic>
 #include <new>
 
 #include "bse_internal.cuh"
@@ -35,6 +36,7 @@ void free_coarse(bse_coarse* c) {
 
 void free_interp(bse_interp* s) {
     if (!s) return;
+    bse_release_run_state(s);
     void* ptrs[] = {s->d_dE, s->d_Dv, s->d_Dc, s->d_P, s->d_list, s->d_list_start, s->d_hd, s->d_Hv, s->d_Hc,
                     s->d_hc, s->d_Q, s->d_R, s->d_X, s->d_U, s->d_Bop, s->d_part, s->d_vec[0],
                     s->d_vec[1], s->d_vec[2], s->d_part_dot, s->d_part_nrm, s->d_a, s->d_aim, s->d_b, s->d_stop,
@@ -43,15 +45,19 @@ void free_interp(bse_interp* s) {
                     s->d_tc_rowstart, s->d_tc_kinfo, s->d_tc_simg};
     for (void* p : ptrs) cudaFree(p);
     bse_tc_release(s);
-    if (s->graph) cudaGraphExecDestroy(s->graph);
     delete s;
 }
 
 }  // namespace
 
+long long bse_next_serial() {
+    static std::atomic<long long> counter{0};
+    return ++counter;
+}
+
 extern "C" {
 
-int bse_version(void) { return 10000; }
+int bse_version(void) { return 10100; }
 
 int bse_ctx_create(bse_ctx** out, int device, void* cuda_stream) {
     if (!out) return BSE_ERR_ARG;
@@ -82,12 +88,23 @@ int bse_ctx_create(bse_ctx** out, int device, void* cuda_stream) {
         return BSE_ERR_OOM;
     }
     cudaMemset(ctx->d_status, 0, sizeof(int));
+    ctx->serial = bse_next_serial();
+    // Load the library's device module and look up the no-allocation scratch
+    // here, at set-up, so that bse_apply_h_noalloc never triggers the lazy
+    // module load (and its allocation) itself.
+    if (bse_noalloc_prepare(ctx) != BSE_OK) {
+        cudaFree(ctx->d_status);
+        if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+        delete ctx;
+        return BSE_ERR_CUDA;
+    }
     *out = ctx;
     return BSE_OK;
 }
 
 void bse_ctx_destroy(bse_ctx* ctx) {
     if (!ctx) return;
+    bse_release_ctx_state(ctx);
     cudaFree(ctx->d_status);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -95,7 +112,8 @@ void bse_ctx_destroy(bse_ctx* ctx) {
 
 const char* bse_last_error(const bse_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
-int bse_build_coarse(bse_ctx* ctx, const bse_model* m, int n_coarse, int kc_prec, bse_coarse** out) {
+int bse_build_coarse(bse_ctx* ctx, const bse_model* m, int n_coarse, int kc_prec, const void* user_kc,
+                     bse_coarse** out) {
     if (!ctx || !out) return BSE_ERR_ARG;
     *out = nullptr;
     if (!m) return set_arg_error(ctx, "model is NULL");
@@ -132,7 +150,7 @@ int bse_build_coarse(bse_ctx* ctx, const bse_model* m, int n_coarse, int kc_prec
         (rc = upload(ctx, &c->d_gen_c, m->gen_c, 12 * nc * nc, "gen_c")) != BSE_OK ||
         (rc = upload(ctx, &c->d_mu, m->mu, 2 * 7 * 26 * nv * nc, "mu")) != BSE_OK ||
         (rc = upload(ctx, &c->d_dip, m->dip, 2 * 7 * 3 * nv * nc, "dip")) != BSE_OK ||
-        (rc = bse_setup_coarse_device(ctx, c)) != BSE_OK) {
+        (rc = bse_setup_coarse_device(ctx, c, user_kc)) != BSE_OK) {
         free_coarse(c);
         return rc;
     }
@@ -167,7 +185,7 @@ int bse_coarse_get_kc(bse_ctx* ctx, const bse_coarse* c, double* host_kc) {
 void bse_free_coarse(bse_coarse* c) { free_coarse(c); }
 
 int bse_interp_setup(bse_ctx* ctx, const bse_coarse* c, int n_div, int scheme, double width_w, int vec_prec,
-                     bse_interp** out) {
+                     const bse_dense_inputs* dense, bse_interp** out) {
     if (!ctx || !out) return BSE_ERR_ARG;
     *out = nullptr;
     if (!c) return set_arg_error(ctx, "coarse handle is NULL");
@@ -186,6 +204,13 @@ int bse_interp_setup(bse_ctx* ctx, const bse_coarse* c, int n_div, int scheme, d
     }
     const long long nk = (long long)c->nkc * n_div * n_div * n_div;
     if (nk * c->t > (1LL << 31) - 1) { ctx->err = "dense dimension above 2^31"; return BSE_ERR_UNSUPPORTED; }
+    if (dense) {
+        const size_t N = (size_t)nk * c->t;
+        if ((dense->dE && !finite_arr(dense->dE, N)) || (dense->P && !finite_arr(dense->P, 6 * N)) ||
+            (dense->Dv && !finite_arr(dense->Dv, 16 * (size_t)nk * c->nv * c->nv)) ||
+            (dense->Dc && !finite_arr(dense->Dc, 16 * (size_t)nk * c->nc * c->nc)))
+            return set_arg_error(ctx, "non-finite entry in the dense inputs");
+    }
     if (cudaSetDevice(ctx->device) != cudaSuccess) return BSE_ERR_CUDA;
     bse_interp* s = new (std::nothrow) bse_interp();
     if (!s) return BSE_ERR_OOM;
@@ -193,7 +218,8 @@ int bse_interp_setup(bse_ctx* ctx, const bse_coarse* c, int n_div, int scheme, d
     s->nv = c->nv; s->nc = c->nc; s->t = c->t; s->N = (int)(nk * c->t);
     s->scheme = base; s->nb1 = (scheme & BSE_NB1) ? 1 : 0; s->vec_prec = vec_prec; s->width = width_w;
     s->nf_force_cuda_cores = (scheme & BSE_NF_CUDA_CORES) ? 1 : 0;
-    int rc = bse_setup_interp_device(ctx, s);
+    s->serial = bse_next_serial();
+    int rc = bse_setup_interp_device(ctx, s, dense);
     if (rc != BSE_OK) { free_interp(s); return rc; }
     *out = s;
     return BSE_OK;
@@ -226,7 +252,10 @@ int bse_haydock_run(bse_ctx* ctx, bse_interp* const* sys, int nsys, const int* n
     if (!ctx || !sys || !npol || !pol_dirs || !a || !b || !pnorm2 || !steps_done) return BSE_ERR_ARG;
     if (nsys < 1) return set_arg_error(ctx, "nsys must be >= 1");
     if (nsteps < 1 || nsteps > 100000) return set_arg_error(ctx, "nsteps must be in 1..100000");
-    if (flags & ~(BSE_REORTH_CGS2 | BSE_USE_GRAPH | BSE_PROFILE)) return set_arg_error(ctx, "unknown flag");
+    if (flags & ~(BSE_REORTH_CGS2 | BSE_USE_GRAPH | BSE_PROFILE | BSE_STOP_CONVERGED))
+        return set_arg_error(ctx, "unknown flag");
+    if ((flags & BSE_STOP_CONVERGED) && !ctx->stop_set)
+        return set_arg_error(ctx, "BSE_STOP_CONVERGED needs a rule (bse_set_stop_rule)");
     int total = 0;
     for (int i = 0; i < nsys; ++i) {
         if (!sys[i]) return set_arg_error(ctx, "system handle is NULL");
@@ -249,6 +278,30 @@ int bse_haydock_run(bse_ctx* ctx, bse_interp* const* sys, int nsys, const int* n
         off += npol[i];
     }
     return worst;
+}
+
+int bse_set_stop_rule(bse_ctx* ctx, double tol, int check_every, double s_eps, double eta, int nw,
+                      const double* omega) {
+    if (!ctx || !omega) return BSE_ERR_ARG;
+    const double sc[] = {tol, s_eps, eta};
+    if (!finite_arr(sc, 3) || tol <= 0.0 || eta <= 0.0 || check_every < 1 || nw < 1 || !finite_arr(omega, nw))
+        return set_arg_error(ctx, "stop rule needs tol > 0, check_every >= 1, eta > 0, nw >= 1, finite numbers");
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return BSE_ERR_CUDA;
+    if (nw > ctx->stop_nw) {
+        cudaFree(ctx->d_stop_omega);
+        ctx->d_stop_omega = nullptr;
+        ctx->stop_nw = 0;
+        int rc = bse_alloc(ctx, (void**)&ctx->d_stop_omega, sizeof(double) * nw, "stop-rule frequencies");
+        if (rc != BSE_OK) return rc;
+    }
+    BSE_CUDA_TRY(ctx, cudaMemcpy(ctx->d_stop_omega, omega, sizeof(double) * nw, cudaMemcpyHostToDevice));
+    ctx->stop_nw = nw;
+    ctx->stop_tol = tol;
+    ctx->stop_every = check_every;
+    ctx->stop_seps = s_eps;
+    ctx->stop_eta = eta;
+    ctx->stop_set = 1;
+    return BSE_OK;
 }
 
 int bse_last_kernel_times(const bse_ctx* ctx, double* ms, long long* counts) {

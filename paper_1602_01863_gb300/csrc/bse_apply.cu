@@ -1464,35 +1464,134 @@ int apply_h_typed(bse_ctx* ctx, bse_interp* s, int nchains, const void* psi_v, v
     return BSE_OK;
 }
 
+// Convergence check of the Sec. 5.1 stopping rule (BSE_STOP_CONVERGED): eps on
+// the rule's frequencies from the first `ms` steps (Eq. fraccont, bottom-up,
+// FP64, as k_cont_frac), against the previous check's eps, which it replaces.
+// Block maxima of |d Re eps|, |Re eps|, |d Im eps|, |Im eps| go to `part`.
+constexpr int kConvThreads = 64;
+__global__ void __launch_bounds__(kConvThreads) k_conv_eval(const double* __restrict__ a, const double* __restrict__ b,
+                                                            int ms, int m, const double* __restrict__ pn2, double pref,
+                                                            double eta, const double* __restrict__ omega, int nw,
+                                                            double2* __restrict__ eps_prev, double* __restrict__ part,
+                                                            const int* __restrict__ stop) {
+    __shared__ double red[4][kConvThreads];
+    const int ch = blockIdx.y;
+    if (stop[ch]) return;                                        // uniform over the block
+    const int iw = blockIdx.x * kConvThreads + threadIdx.x;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    if (iw < nw) {
+        const double zr = omega[iw], zi = eta;
+        double gr = 0.0, gi = 0.0;
+        for (int i = ms - 1; i >= 0; --i) {
+            const double bb = (i == ms - 1) ? 0.0 : b[ch * (m + 1) + i + 1];
+            const double b2 = bb * bb;
+            const double dr = zr - a[ch * m + i] - b2 * gr, di = zi - b2 * gi;
+            const double den = dr * dr + di * di;
+            gr = dr / den;
+            gi = -di / den;
+        }
+        const double2 e = make_double2(1.0 - pref * pn2[ch] * gr, -pref * pn2[ch] * gi);
+        const double2 o = eps_prev[(size_t)ch * nw + iw];
+        eps_prev[(size_t)ch * nw + iw] = e;
+        v[0] = fabs(e.x - o.x);
+        v[1] = fabs(e.x);
+        v[2] = fabs(e.y - o.y);
+        v[3] = fabs(e.y);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) red[q][threadIdx.x] = v[q];
+    __syncthreads();
+    for (int s = kConvThreads / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) red[q][threadIdx.x] = fmax(red[q][threadIdx.x], red[q][threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) part[((size_t)ch * gridDim.x + blockIdx.x) * 4 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// Stop decision: a chain whose spectrum moved by at most tol (relative to its
+// largest |Re eps| and |Im eps|) since the previous check stops after `ms`
+// steps; the stop word records -ms (a breakdown records +steps).
+__global__ void k_conv_decide(const double* __restrict__ part, int nblk, int ms, int first, double tol,
+                              int* __restrict__ stop) {
+    const int ch = blockIdx.x;
+    if (threadIdx.x != 0 || stop[ch]) return;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = 0; i < nblk; ++i)
+        for (int q = 0; q < 4; ++q) v[q] = fmax(v[q], part[((size_t)ch * nblk + i) * 4 + q]);
+    if (!first && v[0] <= tol * v[1] && v[2] <= tol * v[3]) stop[ch] = -ms;
+}
+
+// The stopping rule as one system's run sees it (prefactor s_eps / N_k).
+struct StopRule {
+    double tol, pref, eta;
+    int every, nw;
+    const double* omega;
+};
+
+inline StopRule stop_rule_for(const bse_ctx* ctx, const bse_interp* s) {
+    return StopRule{ctx->stop_tol, ctx->stop_seps / (double)s->nk, ctx->stop_eta, ctx->stop_every, ctx->stop_nw,
+                    ctx->d_stop_omega};
+}
+
+void drop_graph(bse_interp* s) {
+    if (s->graph) cudaGraphExecDestroy(s->graph);
+    s->graph = nullptr;
+    ++s->state_serial;
+}
+
+// Buffers of a Haydock run, kept in the handle: coefficients for m steps, the
+// start directions and norms, the CGS2 basis, the convergence-check state for
+// nw frequencies.  Replacing any of them invalidates a cached graph.
 template <typename T>
-int ensure_state(bse_ctx* ctx, bse_interp* s, int m, bool reorth) {
+int ensure_state(bse_ctx* ctx, bse_interp* s, int m, bool reorth, int nw) {
     using V = typename Cx<T>::V;
+    int rc;
+    if (!s->d_dirs) {
+        if ((rc = bse_alloc(ctx, (void**)&s->d_dirs, sizeof(double) * 3 * BSE_MAX_CHAINS, "directions")) != BSE_OK) return rc;
+        if ((rc = bse_alloc(ctx, (void**)&s->d_pn2, sizeof(double) * BSE_MAX_CHAINS, "norms")) != BSE_OK) return rc;
+    }
     if (s->m_alloc < m) {
+        drop_graph(s);
         cudaFree(s->d_a); cudaFree(s->d_aim); cudaFree(s->d_b);
         s->d_a = s->d_aim = s->d_b = nullptr;
         s->m_alloc = 0;
-        int rc;
         if ((rc = bse_alloc(ctx, (void**)&s->d_a, sizeof(double) * BSE_MAX_CHAINS * m, "a")) != BSE_OK) return rc;
         if ((rc = bse_alloc(ctx, (void**)&s->d_aim, sizeof(double) * BSE_MAX_CHAINS * m, "a imag")) != BSE_OK) return rc;
         if ((rc = bse_alloc(ctx, (void**)&s->d_b, sizeof(double) * BSE_MAX_CHAINS * (m + 1), "b")) != BSE_OK) return rc;
         s->m_alloc = m;
     }
     if (reorth && s->basis_m < m + 1) {
+        drop_graph(s);
         cudaFree(s->d_basis); cudaFree(s->d_cgs_part); cudaFree(s->d_cgs_h);
         s->d_basis = nullptr; s->d_cgs_part = s->d_cgs_h = nullptr;
         s->basis_m = 0;
-        int rc;
         if ((rc = bse_alloc(ctx, &s->d_basis, sizeof(V) * BSE_MAX_CHAINS * (size_t)(m + 1) * s->N, "Lanczos basis")) != BSE_OK) return rc;
         if ((rc = bse_alloc(ctx, (void**)&s->d_cgs_part, sizeof(double2) * (size_t)(m + 1) * BSE_MAX_VEC_BLOCKS, "CGS partials")) != BSE_OK) return rc;
         if ((rc = bse_alloc(ctx, (void**)&s->d_cgs_h, sizeof(double2) * (size_t)(m + 1), "CGS coefficients")) != BSE_OK) return rc;
         s->basis_m = m + 1;
     }
+    if (nw > s->eps_nw) {
+        drop_graph(s);
+        cudaFree(s->d_eps_prev); cudaFree(s->d_conv_part);
+        s->d_eps_prev = nullptr; s->d_conv_part = nullptr;
+        s->eps_nw = 0;
+        const int nblk = (nw + kConvThreads - 1) / kConvThreads;
+        if ((rc = bse_alloc(ctx, (void**)&s->d_eps_prev, sizeof(double2) * BSE_MAX_CHAINS * (size_t)nw, "previous spectrum")) != BSE_OK) return rc;
+        if ((rc = bse_alloc(ctx, (void**)&s->d_conv_part, sizeof(double) * BSE_MAX_CHAINS * 4 * (size_t)nblk, "check maxima")) != BSE_OK) return rc;
+        s->eps_nw = nw;
+    }
     return BSE_OK;
 }
 
-// Enqueue the whole Haydock loop for one system on ctx->stream.
+// Enqueue the whole Haydock loop for one system on ctx->stream (start vectors
+// from s->d_dirs).  With a stopping rule the convergence check runs every
+// rule->every steps; with `poll` the host reads the stop words after each
+// check and stops enqueueing once every chain has stopped.
 template <typename T>
-int enqueue_chains(bse_ctx* ctx, bse_interp* s, int nch, const double* d_dirs, double* d_pn2, int m, bool reorth, bool prof) {
+int enqueue_chains(bse_ctx* ctx, bse_interp* s, int nch, int m, bool reorth, bool prof, const StopRule* rule,
+                   bool poll) {
     using V = typename Cx<T>::V;
     cudaStream_t st = ctx->stream;
     const int N = s->N;
@@ -1507,9 +1606,9 @@ int enqueue_chains(bse_ctx* ctx, bse_interp* s, int nch, const double* d_dirs, d
     const int nb4 = (int)std::min<long long>(std::max<long long>((N / 2 + 255) / 256, 1), BSE_MAX_VEC_BLOCKS);
     cudaMemsetAsync(s->d_stop, 0, sizeof(int) * BSE_MAX_CHAINS, st);
     // psi_1 = P / ||P|| in B, psi_0 = 0 in A
-    k_dipole_start<T><<<nb, BSE_VEC_THREADS, 0, st>>>(s->d_P, d_dirs, N, nch, B, s->d_part_nrm);
-    k_start_norm<T><<<nch, 256, 0, st>>>(s->d_part_nrm, nb, m, d_pn2, s->d_b);
-    k_start_scale<T><<<nb, BSE_VEC_THREADS, 0, st>>>(B, d_pn2, N, nch, A, basis, mb);
+    k_dipole_start<T><<<nb, BSE_VEC_THREADS, 0, st>>>(s->d_P, s->d_dirs, N, nch, B, s->d_part_nrm);
+    k_start_norm<T><<<nch, 256, 0, st>>>(s->d_part_nrm, nb, m, s->d_pn2, s->d_b);
+    k_start_scale<T><<<nb, BSE_VEC_THREADS, 0, st>>>(B, s->d_pn2, N, nch, A, basis, mb);
     for (int i = 0; i < m; ++i) {
         int rc = apply_h_typed<T>(ctx, s, nch, B, W, prof);
         if (rc != BSE_OK) return rc;
@@ -1530,12 +1629,67 @@ int enqueue_chains(bse_ctx* ctx, bse_interp* s, int nch, const double* d_dirs, d
                 }
         }
         k_reduce_b<<<nch, 256, 0, st>>>(s->d_part_nrm, (vec4 && !reorth) ? nb4 : nb, i, m, s->d_a, s->d_b, s->d_stop);
+        if (rule && (i + 1) % rule->every == 0) {
+            const int nblk = (rule->nw + kConvThreads - 1) / kConvThreads;
+            k_conv_eval<<<dim3(nblk, nch), kConvThreads, 0, st>>>(s->d_a, s->d_b, i + 1, m, s->d_pn2, rule->pref, rule->eta,
+                                                                  rule->omega, rule->nw, s->d_eps_prev, s->d_conv_part,
+                                                                  s->d_stop);
+            k_conv_decide<<<nch, 32, 0, st>>>(s->d_conv_part, nblk, i + 1, (i + 1) == rule->every ? 1 : 0, rule->tol,
+                                              s->d_stop);
+        }
         if (vec4)
             k_lanczos_scale4<<<nb4, 256, 0, st>>>((const float4*)W, (float4*)A, s->d_b, i, m, N / 2, nch, (float4*)basis,
                                                   mb, s->d_stop);
         else
             k_lanczos_scale<T><<<nb, BSE_VEC_THREADS, 0, st>>>(W, A, s->d_b, i, m, N, nch, basis, mb, s->d_stop);
         std::swap(A, B);
+        if (poll && rule && (i + 1) % rule->every == 0) {
+            int stop[BSE_MAX_CHAINS] = {0, 0, 0, 0};
+            BSE_CUDA_TRY(ctx, cudaMemcpyAsync(stop, s->d_stop, sizeof(int) * BSE_MAX_CHAINS, cudaMemcpyDeviceToHost, st));
+            BSE_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+            bool all = true;
+            for (int ch = 0; ch < nch; ++ch) all = all && stop[ch] != 0;
+            if (all) break;
+        }
+    }
+    return BSE_OK;
+}
+
+// Copy a run's results to the host; steps_done from the stop words (+k: a
+// breakdown after k steps, -k: converged after k steps, 0: all m steps).
+int finish_run(bse_ctx* ctx, bse_interp* s, int nch, int m, double* a, double* b, double* pnorm2, int* steps_done,
+               int* warn) {
+    cudaStream_t st = ctx->stream;
+    int stop[BSE_MAX_CHAINS] = {0, 0, 0, 0};
+    cudaMemcpyAsync(pnorm2, s->d_pn2, sizeof(double) * nch, cudaMemcpyDeviceToHost, st);
+    for (int ch = 0; ch < nch; ++ch) {
+        cudaMemcpyAsync(a + (size_t)ch * m, s->d_a + (size_t)ch * m, sizeof(double) * m, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(b + (size_t)ch * (m + 1), s->d_b + (size_t)ch * (m + 1), sizeof(double) * (m + 1), cudaMemcpyDeviceToHost, st);
+    }
+    cudaMemcpyAsync(stop, s->d_stop, sizeof(int) * BSE_MAX_CHAINS, cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        ctx->err = std::string("Haydock run: ") + cudaGetErrorString(e);
+        return BSE_ERR_CUDA;
+    }
+    for (int ch = 0; ch < nch; ++ch) {
+        steps_done[ch] = stop[ch] > 0 ? stop[ch] : (stop[ch] < 0 ? -stop[ch] : m);
+        if (stop[ch] > 0) *warn = BSE_WARN_BREAKDOWN;
+        // coefficients past the last step are left undefined on the device: zero them
+        for (int i = steps_done[ch]; i < m; ++i) a[(size_t)ch * m + i] = 0.0;
+        for (int i = steps_done[ch] + 1; i <= m; ++i) b[(size_t)ch * (m + 1) + i] = 0.0;
+    }
+    return BSE_OK;
+}
+
+int read_status(bse_ctx* ctx) {
+    int status = 0;
+    BSE_CUDA_TRY(ctx, cudaMemcpy(&status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status != 0) {
+        ctx->err = bse_timeout_message(status);
+        cudaMemset(ctx->d_status, 0, sizeof(int));
+        return BSE_ERR_TIMEOUT;
     }
     return BSE_OK;
 }
@@ -1545,90 +1699,91 @@ int run_chains_typed(bse_ctx* ctx, bse_interp* s, int nch, const double* pol_dir
                      double* b, double* pnorm2, int* steps_done) {
     const bool reorth = flags & BSE_REORTH_CGS2;
     const bool prof = flags & BSE_PROFILE;
-    const bool graph = (flags & BSE_USE_GRAPH) && !prof;
-    int rc = ensure_state<T>(ctx, s, m, reorth);
+    const bool conv = flags & BSE_STOP_CONVERGED;
+    const bool graph = (flags & BSE_USE_GRAPH) && !prof && !conv;
+    int rc = ensure_state<T>(ctx, s, m, reorth, conv ? ctx->stop_nw : 0);
     if (rc != BSE_OK) return rc;
     cudaStream_t st = ctx->stream;
-    double* d_dirs = nullptr;
-    double* d_pn2 = nullptr;
-    // small per-run buffers live in the handle's Q scratch tail? keep them separate and explicit
-    if ((rc = bse_alloc(ctx, (void**)&d_dirs, sizeof(double) * 3 * BSE_MAX_CHAINS, "directions")) != BSE_OK) return rc;
-    if ((rc = bse_alloc(ctx, (void**)&d_pn2, sizeof(double) * BSE_MAX_CHAINS, "norms")) != BSE_OK) { cudaFree(d_dirs); return rc; }
-    BSE_CUDA_TRY(ctx, cudaMemcpyAsync(d_dirs, pol_dirs, sizeof(double) * 3 * nch, cudaMemcpyHostToDevice, st));
+    BSE_CUDA_TRY(ctx, cudaMemcpyAsync(s->d_dirs, pol_dirs, sizeof(double) * 3 * nch, cudaMemcpyHostToDevice, st));
     if (prof) for (int k = 0; k < KC_COUNT; ++k) { ctx->kt_ms[k] = 0; ctx->kt_n[k] = 0; }
     if (graph) {
-        cudaGraph_t g = nullptr;
-        cudaGraphExec_t ge = nullptr;
-        cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) {
-            rc = enqueue_chains<T>(ctx, s, nch, d_dirs, d_pn2, m, reorth, false);
-            e = cudaStreamEndCapture(st, &g);
+        const long long key[5] = {ctx->serial, nch, m, flags & (BSE_REORTH_CGS2 | BSE_USE_GRAPH), s->state_serial};
+        if (!s->graph || !std::equal(key, key + 5, s->graph_key)) {
+            if (s->graph) cudaGraphExecDestroy(s->graph);
+            s->graph = nullptr;
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                rc = enqueue_chains<T>(ctx, s, nch, m, reorth, false, nullptr, false);
+                e = cudaStreamEndCapture(st, &g);
+            }
+            if (e == cudaSuccess && rc == BSE_OK) e = cudaGraphInstantiate(&s->graph, g, 0);
+            if (g) cudaGraphDestroy(g);
+            if (rc != BSE_OK) return rc;
+            if (e != cudaSuccess) {
+                s->graph = nullptr;
+                ctx->err = std::string("graph capture: ") + cudaGetErrorString(e);
+                return BSE_ERR_CUDA;
+            }
+            std::copy(key, key + 5, s->graph_key);
         }
-        if (e == cudaSuccess && rc == BSE_OK) e = cudaGraphInstantiate(&ge, g, 0);
-        if (e == cudaSuccess && rc == BSE_OK) e = cudaGraphLaunch(ge, st);
-        if (ge) cudaGraphExecDestroy(ge);
-        if (g) cudaGraphDestroy(g);
-        if (e != cudaSuccess) {
-            cudaFree(d_dirs); cudaFree(d_pn2);
-            ctx->err = std::string("graph capture/launch: ") + cudaGetErrorString(e);
-            return BSE_ERR_CUDA;
-        }
+        BSE_CUDA_TRY(ctx, cudaGraphLaunch(s->graph, st));
     } else {
-        rc = enqueue_chains<T>(ctx, s, nch, d_dirs, d_pn2, m, reorth, prof);
-    }
-    if (rc != BSE_OK) { cudaFree(d_dirs); cudaFree(d_pn2); return rc; }
-    std::vector<int> stop(BSE_MAX_CHAINS);
-    int status = 0;
-    cudaMemcpyAsync(pnorm2, d_pn2, sizeof(double) * nch, cudaMemcpyDeviceToHost, st);
-    for (int ch = 0; ch < nch; ++ch) {
-        cudaMemcpyAsync(a + (size_t)ch * m, s->d_a + (size_t)ch * m, sizeof(double) * m, cudaMemcpyDeviceToHost, st);
-        cudaMemcpyAsync(b + (size_t)ch * (m + 1), s->d_b + (size_t)ch * (m + 1), sizeof(double) * (m + 1), cudaMemcpyDeviceToHost, st);
-    }
-    cudaMemcpyAsync(stop.data(), s->d_stop, sizeof(int) * BSE_MAX_CHAINS, cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(&status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st);
-    cudaError_t e = cudaStreamSynchronize(st);
-    cudaFree(d_dirs);
-    cudaFree(d_pn2);
-    if (e == cudaSuccess) e = cudaGetLastError();
-    if (e != cudaSuccess) {
-        ctx->err = std::string("Haydock run: ") + cudaGetErrorString(e);
-        return BSE_ERR_CUDA;
-    }
-    if (status != 0) {
-        ctx->err = bse_timeout_message(status);
-        cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st);
-        return BSE_ERR_TIMEOUT;
+        StopRule rule{};
+        if (conv) rule = stop_rule_for(ctx, s);
+        rc = enqueue_chains<T>(ctx, s, nch, m, reorth, prof, conv ? &rule : nullptr, conv);
+        if (rc != BSE_OK) return rc;
     }
     int warn = BSE_OK;
-    for (int ch = 0; ch < nch; ++ch) {
-        steps_done[ch] = stop[ch] ? stop[ch] : m;
-        if (stop[ch]) warn = BSE_WARN_BREAKDOWN;
-    }
+    if ((rc = finish_run(ctx, s, nch, m, a, b, pnorm2, steps_done, &warn)) != BSE_OK) return rc;
+    if ((rc = read_status(ctx)) != BSE_OK) return rc;
     return warn;
 }
 
 template <typename T>
 int dipoles_typed(bse_ctx* ctx, bse_interp* s, int npol, const double* pol_dirs, void* p_out, double* pnorm2) {
     cudaStream_t st = ctx->stream;
-    double* d_dirs = nullptr;
-    double* d_pn2 = nullptr;
-    int rc;
-    if ((rc = bse_alloc(ctx, (void**)&d_dirs, sizeof(double) * 3 * BSE_MAX_CHAINS, "directions")) != BSE_OK) return rc;
-    if ((rc = bse_alloc(ctx, (void**)&d_pn2, sizeof(double) * BSE_MAX_CHAINS, "norms")) != BSE_OK) { cudaFree(d_dirs); return rc; }
-    cudaMemcpyAsync(d_dirs, pol_dirs, sizeof(double) * 3 * npol, cudaMemcpyHostToDevice, st);
+    int rc = ensure_state<T>(ctx, s, 1, false, 0);
+    if (rc != BSE_OK) return rc;
+    cudaMemcpyAsync(s->d_dirs, pol_dirs, sizeof(double) * 3 * npol, cudaMemcpyHostToDevice, st);
     const int nb = vec_blocks(s->N);
-    k_dipole_start<T><<<nb, BSE_VEC_THREADS, 0, st>>>(s->d_P, d_dirs, s->N, npol, (typename Cx<T>::V*)p_out, s->d_part_nrm);
-    k_start_norm<T><<<npol, 256, 0, st>>>(s->d_part_nrm, nb, 0, d_pn2, nullptr);
-    cudaMemcpyAsync(pnorm2, d_pn2, sizeof(double) * npol, cudaMemcpyDeviceToHost, st);
+    k_dipole_start<T><<<nb, BSE_VEC_THREADS, 0, st>>>(s->d_P, s->d_dirs, s->N, npol, (typename Cx<T>::V*)p_out, s->d_part_nrm);
+    k_start_norm<T><<<npol, 256, 0, st>>>(s->d_part_nrm, nb, 0, s->d_pn2, nullptr);
+    cudaMemcpyAsync(pnorm2, s->d_pn2, sizeof(double) * npol, cudaMemcpyDeviceToHost, st);
     cudaError_t e = cudaStreamSynchronize(st);
-    cudaFree(d_dirs);
-    cudaFree(d_pn2);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) { ctx->err = std::string("dipoles: ") + cudaGetErrorString(e); return BSE_ERR_CUDA; }
     return BSE_OK;
 }
 
 }  // namespace
+
+void bse_release_run_state(bse_interp* s) {
+    if (s->graph) cudaGraphExecDestroy(s->graph);
+    s->graph = nullptr;
+    cudaFree(s->d_dirs); cudaFree(s->d_pn2); cudaFree(s->d_eps_prev); cudaFree(s->d_conv_part);
+    s->d_dirs = nullptr; s->d_pn2 = nullptr; s->d_eps_prev = nullptr; s->d_conv_part = nullptr;
+}
+
+void bse_release_ctx_state(bse_ctx* ctx) {
+    if (ctx->batch_graph) cudaGraphExecDestroy(ctx->batch_graph);
+    ctx->batch_graph = nullptr;
+    for (int k = 0; k < 8; ++k) {
+        if (ctx->side[k]) cudaStreamDestroy(ctx->side[k]);
+        if (ctx->side_join[k]) cudaEventDestroy(ctx->side_join[k]);
+        ctx->side[k] = nullptr;
+        ctx->side_join[k] = nullptr;
+    }
+    if (ctx->side_fork) cudaEventDestroy(ctx->side_fork);
+    ctx->side_fork = nullptr;
+    cudaFree(ctx->cf_buf);
+    ctx->cf_buf = nullptr;
+    ctx->cf_bytes = 0;
+    cudaFree(ctx->d_stop_omega);
+    ctx->d_stop_omega = nullptr;
+}
+
+void bse_invalidate_graph(bse_interp* s) { drop_graph(s); }
 
 int bse_apply_once(bse_ctx* ctx, bse_interp* s, int nvec, const void* x, void* y, bool profile) {
     int rc = (s->vec_prec == BSE_PREC_F64) ? apply_h_typed<double>(ctx, s, nvec, x, y, profile)
@@ -1637,14 +1792,7 @@ int bse_apply_once(bse_ctx* ctx, bse_interp* s, int nvec, const void* x, void* y
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) { ctx->err = std::string("apply H: ") + cudaGetErrorString(e); return BSE_ERR_CUDA; }
-    int status = 0;
-    cudaMemcpy(&status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost);
-    if (status) {
-        cudaMemset(ctx->d_status, 0, sizeof(int));
-        ctx->err = bse_timeout_message(status);
-        return BSE_ERR_TIMEOUT;
-    }
-    return BSE_OK;
+    return read_status(ctx);
 }
 
 int bse_run_chains(bse_ctx* ctx, bse_interp* s, int npol, const double* pol_dirs, int nsteps, int flags, double* a,
@@ -1658,110 +1806,105 @@ int bse_run_chains(bse_ctx* ctx, bse_interp* s, int npol, const double* pol_dirs
 // loop is captured on one of up to 8 side streams forked from the context
 // stream (longest systems first, each onto the least-loaded stream) and
 // joined back, so the batch is a single graph launch whose branches run
-// concurrently on the GPU.
+// concurrently on the GPU.  The instantiated graph stays in the context and is
+// replayed while the same systems (by serial), chain counts, steps and flags
+// come back; with BSE_STOP_CONVERGED the stopped chains skip their work.
 int bse_run_batch(bse_ctx* ctx, bse_interp* const* sys, int nsys, const int* npol, const double* pol_dirs, int m,
                   int flags, double* a, double* b, double* pnorm2, int* steps_done) {
     const bool reorth = flags & BSE_REORTH_CGS2;
+    const bool conv = flags & BSE_STOP_CONVERGED;
     cudaStream_t main_st = ctx->stream;
-    std::vector<double*> d_dirs(nsys, nullptr), d_pn2(nsys, nullptr);
     std::vector<int> first(nsys);
     int rc = BSE_OK, off = 0;
-    auto cleanup = [&]() {
-        for (int i = 0; i < nsys; ++i) { cudaFree(d_dirs[i]); cudaFree(d_pn2[i]); }
-    };
+    std::vector<long long> key = {ctx->serial, m, flags, conv ? (long long)ctx->stop_every : 0};
     for (int i = 0; i < nsys; ++i) {
         bse_interp* s = sys[i];
-        rc = (s->vec_prec == BSE_PREC_F64) ? ensure_state<double>(ctx, s, m, reorth) : ensure_state<float>(ctx, s, m, reorth);
-        if (rc == BSE_OK) rc = bse_alloc(ctx, (void**)&d_dirs[i], sizeof(double) * 3 * BSE_MAX_CHAINS, "directions");
-        if (rc == BSE_OK) rc = bse_alloc(ctx, (void**)&d_pn2[i], sizeof(double) * BSE_MAX_CHAINS, "norms");
-        if (rc != BSE_OK) { cleanup(); return rc; }
-        cudaMemcpyAsync(d_dirs[i], pol_dirs + 3 * off, sizeof(double) * 3 * npol[i], cudaMemcpyHostToDevice, main_st);
+        rc = (s->vec_prec == BSE_PREC_F64) ? ensure_state<double>(ctx, s, m, reorth, conv ? ctx->stop_nw : 0)
+                                           : ensure_state<float>(ctx, s, m, reorth, conv ? ctx->stop_nw : 0);
+        if (rc != BSE_OK) return rc;
+        BSE_CUDA_TRY(ctx, cudaMemcpyAsync(s->d_dirs, pol_dirs + 3 * off, sizeof(double) * 3 * npol[i],
+                                          cudaMemcpyHostToDevice, main_st));
         first[i] = off;
         off += npol[i];
+        key.push_back(s->serial);
+        key.push_back(s->state_serial);
+        key.push_back(npol[i]);
+    }
+    if (conv) {
+        // the rule's numbers are baked into the captured kernels
+        long long bits[3];
+        std::memcpy(&bits[0], &ctx->stop_tol, 8);
+        std::memcpy(&bits[1], &ctx->stop_seps, 8);
+        std::memcpy(&bits[2], &ctx->stop_eta, 8);
+        key.insert(key.end(), bits, bits + 3);
+        key.push_back(ctx->stop_nw);
+        key.push_back((long long)(uintptr_t)ctx->d_stop_omega);
     }
     const int K = std::min(nsys, 8);
-    std::vector<cudaStream_t> side(K, nullptr);
-    std::vector<cudaEvent_t> join(K, nullptr);
-    cudaEvent_t fork = nullptr;
-    cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
-    for (int k = 0; k < K; ++k) {
-        cudaStreamCreateWithFlags(&side[k], cudaStreamNonBlocking);
-        cudaEventCreateWithFlags(&join[k], cudaEventDisableTiming);
-    }
-    std::vector<int> order(nsys);
-    std::vector<double> cost(nsys);
-    for (int i = 0; i < nsys; ++i) {
-        const bse_interp* s = sys[i];
-        order[i] = i;
-        cost[i] = (double)s->co->Nc * s->co->Nc * npol[i] + (double)s->N * npol[i] * 64.0 +
-                  (s->scheme == BSE_SCHEME_M3 ? (double)s->nk * s->npairs * s->t * npol[i] * 8.0 : 0.0);
-    }
-    std::sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
-    cudaGraph_t g = nullptr;
-    cudaGraphExec_t ge = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(main_st, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-        cudaEventRecord(fork, main_st);
-        for (int k = 0; k < K; ++k) cudaStreamWaitEvent(side[k], fork, 0);
-        std::vector<double> load(K, 0.0);
-        for (int i : order) {
-            const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-            load[k] += cost[i];
-            ctx->stream = side[k];
-            rc = (sys[i]->vec_prec == BSE_PREC_F64)
-                     ? enqueue_chains<double>(ctx, sys[i], npol[i], d_dirs[i], d_pn2[i], m, reorth, false)
-                     : enqueue_chains<float>(ctx, sys[i], npol[i], d_dirs[i], d_pn2[i], m, reorth, false);
-            ctx->stream = main_st;
-            if (rc != BSE_OK) break;
+    if (!ctx->side_fork) {
+        BSE_CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->side_fork, cudaEventDisableTiming));
+        for (int k = 0; k < 8; ++k) {
+            BSE_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->side[k], cudaStreamNonBlocking));
+            BSE_CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->side_join[k], cudaEventDisableTiming));
         }
-        for (int k = 0; k < K; ++k) {
-            cudaEventRecord(join[k], side[k]);
-            cudaStreamWaitEvent(main_st, join[k], 0);
-        }
-        e = cudaStreamEndCapture(main_st, &g);
     }
-    ctx->stream = main_st;
-    if (e == cudaSuccess && rc == BSE_OK) e = cudaGraphInstantiate(&ge, g, 0);
-    if (e == cudaSuccess && rc == BSE_OK) e = cudaGraphLaunch(ge, main_st);
-    std::vector<std::vector<int>> stop(nsys, std::vector<int>(BSE_MAX_CHAINS));
-    int status = 0;
-    if (e == cudaSuccess && rc == BSE_OK) {
+    cudaError_t e = cudaSuccess;
+    if (!ctx->batch_graph || key != ctx->batch_key) {
+        if (ctx->batch_graph) cudaGraphExecDestroy(ctx->batch_graph);
+        ctx->batch_graph = nullptr;
+        std::vector<int> order(nsys);
+        std::vector<double> cost(nsys);
         for (int i = 0; i < nsys; ++i) {
             const bse_interp* s = sys[i];
-            const int o = first[i];
-            cudaMemcpyAsync(pnorm2 + o, d_pn2[i], sizeof(double) * npol[i], cudaMemcpyDeviceToHost, main_st);
-            for (int ch = 0; ch < npol[i]; ++ch) {
-                cudaMemcpyAsync(a + (size_t)(o + ch) * m, s->d_a + (size_t)ch * m, sizeof(double) * m, cudaMemcpyDeviceToHost, main_st);
-                cudaMemcpyAsync(b + (size_t)(o + ch) * (m + 1), s->d_b + (size_t)ch * (m + 1), sizeof(double) * (m + 1),
-                                cudaMemcpyDeviceToHost, main_st);
+            order[i] = i;
+            cost[i] = (double)s->co->Nc * s->co->Nc * npol[i] + (double)s->N * npol[i] * 64.0 +
+                      (s->scheme == BSE_SCHEME_M3 ? (double)s->nk * s->npairs * s->t * npol[i] * 8.0 : 0.0);
+        }
+        std::sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+        cudaGraph_t g = nullptr;
+        e = cudaStreamBeginCapture(main_st, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaEventRecord(ctx->side_fork, main_st);
+            for (int k = 0; k < K; ++k) cudaStreamWaitEvent(ctx->side[k], ctx->side_fork, 0);
+            std::vector<double> load(K, 0.0);
+            for (int i : order) {
+                const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+                load[k] += cost[i];
+                ctx->stream = ctx->side[k];
+                StopRule rule{};
+                if (conv) rule = stop_rule_for(ctx, sys[i]);
+                rc = (sys[i]->vec_prec == BSE_PREC_F64)
+                         ? enqueue_chains<double>(ctx, sys[i], npol[i], m, reorth, false, conv ? &rule : nullptr, false)
+                         : enqueue_chains<float>(ctx, sys[i], npol[i], m, reorth, false, conv ? &rule : nullptr, false);
+                ctx->stream = main_st;
+                if (rc != BSE_OK) break;
             }
-            cudaMemcpyAsync(stop[i].data(), s->d_stop, sizeof(int) * BSE_MAX_CHAINS, cudaMemcpyDeviceToHost, main_st);
+            for (int k = 0; k < K; ++k) {
+                cudaEventRecord(ctx->side_join[k], ctx->side[k]);
+                cudaStreamWaitEvent(main_st, ctx->side_join[k], 0);
+            }
+            e = cudaStreamEndCapture(main_st, &g);
         }
-        cudaMemcpyAsync(&status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, main_st);
-        e = cudaStreamSynchronize(main_st);
+        ctx->stream = main_st;
+        if (e == cudaSuccess && rc == BSE_OK) e = cudaGraphInstantiate(&ctx->batch_graph, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (rc != BSE_OK) return rc;
+        if (e != cudaSuccess) {
+            ctx->batch_graph = nullptr;
+            ctx->err = std::string("batched Haydock graph: ") + cudaGetErrorString(e);
+            return BSE_ERR_CUDA;
+        }
+        ctx->batch_key = key;
     }
-    if (ge) cudaGraphExecDestroy(ge);
-    if (g) cudaGraphDestroy(g);
-    for (int k = 0; k < K; ++k) { cudaStreamDestroy(side[k]); cudaEventDestroy(join[k]); }
-    cudaEventDestroy(fork);
-    cleanup();
-    if (rc != BSE_OK) return rc;
-    if (e == cudaSuccess) e = cudaGetLastError();
-    if (e != cudaSuccess) {
-        ctx->err = std::string("batched Haydock graph: ") + cudaGetErrorString(e);
-        return BSE_ERR_CUDA;
-    }
-    if (status != 0) {
-        cudaMemset(ctx->d_status, 0, sizeof(int));
-        ctx->err = bse_timeout_message(status);
-        return BSE_ERR_TIMEOUT;
-    }
+    BSE_CUDA_TRY(ctx, cudaGraphLaunch(ctx->batch_graph, main_st));
     int warn = BSE_OK;
-    for (int i = 0; i < nsys; ++i)
-        for (int ch = 0; ch < npol[i]; ++ch) {
-            steps_done[first[i] + ch] = stop[i][ch] ? stop[i][ch] : m;
-            if (stop[i][ch]) warn = BSE_WARN_BREAKDOWN;
-        }
+    for (int i = 0; i < nsys; ++i) {
+        const int o = first[i];
+        rc = finish_run(ctx, sys[i], npol[i], m, a + (size_t)o * m, b + (size_t)o * (m + 1), pnorm2 + o,
+                        steps_done + o, &warn);
+        if (rc != BSE_OK) return rc;
+    }
+    if ((rc = read_status(ctx)) != BSE_OK) return rc;
     return warn;
 }
 
@@ -1770,19 +1913,30 @@ int bse_make_dipoles(bse_ctx* ctx, bse_interp* s, int npol, const double* pol_di
     return dipoles_typed<float>(ctx, s, npol, pol_dirs, p_out, pnorm2);
 }
 
+// Continued fraction on the device; its buffers are one grow-only block of the
+// context (no allocation once it is large enough).
 int bse_cf_device(bse_ctx* ctx, int nchains, int nsteps, const int* steps_done, const double* a, const double* b,
                   const double* pnorm2, double prefactor, double eta, int nw, const double* omega, double* eps) {
     cudaStream_t st = ctx->stream;
-    double *d_a = nullptr, *d_b = nullptr, *d_pn = nullptr, *d_w = nullptr;
-    int* d_s = nullptr;
-    double2* d_eps = nullptr;
-    int rc = BSE_OK;
-    if ((rc = bse_alloc(ctx, (void**)&d_a, sizeof(double) * nchains * nsteps, "a")) != BSE_OK) return rc;
-    if ((rc = bse_alloc(ctx, (void**)&d_b, sizeof(double) * nchains * (nsteps + 1), "b")) != BSE_OK) goto out;
-    if ((rc = bse_alloc(ctx, (void**)&d_pn, sizeof(double) * nchains, "pnorm2")) != BSE_OK) goto out;
-    if ((rc = bse_alloc(ctx, (void**)&d_w, sizeof(double) * nw, "omega")) != BSE_OK) goto out;
-    if ((rc = bse_alloc(ctx, (void**)&d_s, sizeof(int) * nchains, "steps")) != BSE_OK) goto out;
-    if ((rc = bse_alloc(ctx, (void**)&d_eps, sizeof(double2) * nchains * nw, "eps")) != BSE_OK) goto out;
+    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+    const size_t oa = 0, ob = oa + al(sizeof(double) * nchains * nsteps), op = ob + al(sizeof(double) * nchains * (nsteps + 1));
+    const size_t ow = op + al(sizeof(double) * nchains), os = ow + al(sizeof(double) * nw);
+    const size_t oe = os + al(sizeof(int) * nchains), total = oe + al(sizeof(double2) * nchains * nw);
+    if (total > ctx->cf_bytes) {
+        cudaFree(ctx->cf_buf);
+        ctx->cf_buf = nullptr;
+        ctx->cf_bytes = 0;
+        int rc = bse_alloc(ctx, &ctx->cf_buf, total, "continued-fraction buffers");
+        if (rc != BSE_OK) return rc;
+        ctx->cf_bytes = total;
+    }
+    unsigned char* base = static_cast<unsigned char*>(ctx->cf_buf);
+    double* d_a = (double*)(base + oa);
+    double* d_b = (double*)(base + ob);
+    double* d_pn = (double*)(base + op);
+    double* d_w = (double*)(base + ow);
+    int* d_s = (int*)(base + os);
+    double2* d_eps = (double2*)(base + oe);
     cudaMemcpyAsync(d_a, a, sizeof(double) * nchains * nsteps, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(d_b, b, sizeof(double) * nchains * (nsteps + 1), cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(d_pn, pnorm2, sizeof(double) * nchains, cudaMemcpyHostToDevice, st);
@@ -1790,14 +1944,10 @@ int bse_cf_device(bse_ctx* ctx, int nchains, int nsteps, const int* steps_done, 
     cudaMemcpyAsync(d_s, steps_done, sizeof(int) * nchains, cudaMemcpyHostToDevice, st);
     k_cont_frac<<<(nchains * nw + 127) / 128, 128, 0, st>>>(d_a, d_b, d_s, d_pn, nsteps, nchains, prefactor, eta, nw, d_w, d_eps);
     cudaMemcpyAsync(eps, d_eps, sizeof(double2) * nchains * nw, cudaMemcpyDeviceToHost, st);
-    {
-        cudaError_t e = cudaStreamSynchronize(st);
-        if (e == cudaSuccess) e = cudaGetLastError();
-        if (e != cudaSuccess) { ctx->err = std::string("continued fraction: ") + cudaGetErrorString(e); rc = BSE_ERR_CUDA; }
-    }
-out:
-    cudaFree(d_a); cudaFree(d_b); cudaFree(d_pn); cudaFree(d_w); cudaFree(d_s); cudaFree(d_eps);
-    return rc;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) { ctx->err = std::string("continued fraction: ") + cudaGetErrorString(e); return BSE_ERR_CUDA; }
+    return BSE_OK;
 }
 
 namespace {

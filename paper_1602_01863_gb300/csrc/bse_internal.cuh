@@ -108,6 +108,7 @@ __host__ __device__ inline T interp_weight_as(int js, int l, int nd, int nb1) {
 enum KernelClass { KC_RESTRICT = 0, KC_KCAPPLY = 1, KC_PROLONG = 2, KC_NEAR = 3, KC_LANCZOS = 4, KC_COUNT = 5 };
 
 struct bse_ctx {
+    long long serial = 0;
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;          // created by the context (caller passed NULL)
@@ -116,6 +117,19 @@ struct bse_ctx {
     double kt_ms[KC_COUNT] = {0, 0, 0, 0, 0};
     long long kt_n[KC_COUNT] = {0, 0, 0, 0, 0};
     int sm_count = 0;
+    // stopping rule of BSE_STOP_CONVERGED runs (bse_set_stop_rule)
+    int stop_set = 0, stop_every = 0, stop_nw = 0;
+    double stop_tol = 0, stop_seps = 0, stop_eta = 0;
+    double* d_stop_omega = nullptr;  // [stop_nw]
+    // grow-only scratch of bse_spectrum (no allocation once large enough)
+    void* cf_buf = nullptr;
+    size_t cf_bytes = 0;
+    // batched runs: side streams, events and the cached graph of the last batch
+    cudaStream_t side[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t side_join[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t side_fork = nullptr;
+    cudaGraphExec_t batch_graph = nullptr;
+    std::vector<long long> batch_key;   // serials of the systems, npol, steps, flags
 };
 
 struct bse_coarse {
@@ -196,10 +210,24 @@ struct bse_interp {
     float2* d_lgrid = nullptr;       // 2 x [4][t][L^3] work grids
     float2* d_tw_fwd = nullptr;      // [2 L] twiddles (forward, inverse)
     float2* d_tw_inv = nullptr;
-    // cached graph
+    // per-run buffers (kept: no allocation inside a run once they exist)
+    double* d_dirs = nullptr;        // [4][3] polarisation directions
+    double* d_pn2 = nullptr;         // [4]    ||P||^2
+    double2* d_eps_prev = nullptr;   // [4][eps_nw] spectrum at the previous convergence check
+    double* d_conv_part = nullptr;   // [4][eps_nblk][4] block maxima of a convergence check
+    int eps_nw = 0;
+    // cached graph of the step loop (BSE_USE_GRAPH) and what it was captured for
     cudaGraphExec_t graph = nullptr;
-    int graph_key[4] = {0, 0, 0, 0};
+    long long graph_key[5] = {0, 0, 0, 0, 0};   // context serial, chains, steps, flags, state serial
+    long long serial = 0;            // unique per handle (the batch graph key)
+    long long state_serial = 0;      // bumped whenever buffers a captured graph uses are replaced
 };
+
+// Unique serial numbers for handles and contexts (graph cache keys).
+long long bse_next_serial();
+// Looks up the device address of the no-allocation scratch array on the
+// context's device (bse_noalloc.cu), at context creation.
+int bse_noalloc_prepare(bse_ctx* ctx);
 
 // ----------------------------------------------------------------- helpers
 #define BSE_CUDA_TRY(ctx, call)                                                       \
@@ -221,13 +249,16 @@ inline const char* bse_timeout_message(int status) {
 }
 
 // setup kernels (bse_setup.cu)
-int bse_setup_coarse_device(bse_ctx* ctx, bse_coarse* c);
-int bse_setup_interp_device(bse_ctx* ctx, bse_interp* s);
+int bse_setup_coarse_device(bse_ctx* ctx, bse_coarse* c, const void* user_kc);
+int bse_setup_interp_device(bse_ctx* ctx, bse_interp* s, const bse_dense_inputs* dense);
 
 // hot path (bse_apply.cu)
 int bse_apply_once(bse_ctx* ctx, bse_interp* s, int nvec, const void* x, void* y, bool profile);
 int bse_run_chains(bse_ctx* ctx, bse_interp* s, int npol, const double* pol_dirs, int nsteps,
                    int flags, double* a, double* b, double* pnorm2, int* steps_done);
+void bse_release_run_state(bse_interp* s);
+void bse_invalidate_graph(bse_interp* s);   // a cached step-loop graph no longer matches the handle
+void bse_release_ctx_state(bse_ctx* ctx);
 int bse_run_batch(bse_ctx* ctx, bse_interp* const* sys, int nsys, const int* npol, const double* pol_dirs, int m,
                   int flags, double* a, double* b, double* pnorm2, int* steps_done);
 int bse_make_dipoles(bse_ctx* ctx, bse_interp* s, int npol, const double* pol_dirs, void* p_out,

@@ -755,6 +755,7 @@ int bse_pairs_generate(bse_ctx* ctx, const bse_interp* s, int nblocks, const int
 
 int bse_interp_set_learned(bse_ctx* ctx, bse_interp* s, bse_mlp* m, int radius) {
     if (!ctx || !s) return BSE_ERR_ARG;
+    bse_invalidate_graph(s);                 // the captured step loop changes with the correction
     if (!m) {          // switch the learned correction off
         s->learned = 0;
         return BSE_OK;

@@ -9,12 +9,15 @@
 // bse_interp_setup allocated; this variant takes it from the file-scope
 // array below instead, so after set-up nothing is allocated on any path.
 //
-// The array is a static __device__ object: every GPU that loads the library
-// holds BSE_NOALLOC_SCRATCH_BYTES of it until the process exits.  In host code
-// its name is only a host-side stand-in for the device object, so the device
-// address is looked up with cudaGetSymbolAddress (once per device, on the
-// first call made on that device, with that device current) and passed to
-// the kernels.  That first call should come before any stream capture.
+// The array is a static __device__ object of the library's device module: a
+// device holds BSE_NOALLOC_SCRATCH_BYTES of it from the moment that module is
+// loaded on it until the process exits.  With CUDA's lazy module loading the
+// module loads on first use, and that load allocates; so bse_ctx_create calls
+// bse_noalloc_prepare, which looks up the array's device address
+// (cudaGetSymbolAddress, which loads the module) once per device, with that
+// device current, at set-up.  In host code the array's name is only a
+// host-side stand-in for the device object; the address found here is what
+// the kernels get.  Create the context before any stream capture.
 // Every call shares the one array, which keeps the previous call's contents:
 // the buffers that must start at zero are cleared on each call, and calls
 // that overlap on the GPU (two streams, or two host threads) race on it.
@@ -36,6 +39,20 @@ size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
 }  // namespace
 
+int bse_noalloc_prepare(bse_ctx* ctx) {
+    if (ctx->device < 0 || ctx->device >= BSE_NOALLOC_MAX_DEVICES) return BSE_OK;   // the entry point refuses it
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (g_scratch_addr[ctx->device]) return BSE_OK;
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        ctx->err = std::string("cudaGetSymbolAddress of the static scratch failed: ") + cudaGetErrorString(e);
+        return BSE_ERR_CUDA;
+    }
+    g_scratch_addr[ctx->device] = p;
+    return BSE_OK;
+}
+
 extern "C" int bse_apply_h_noalloc(bse_ctx* ctx, bse_interp* s, int nvec, const void* x, void* y) {
     if (!ctx || !s || !x || !y) return BSE_ERR_ARG;
     if (nvec < 1 || nvec > BSE_MAX_CHAINS) {
@@ -54,16 +71,11 @@ extern "C" int bse_apply_h_noalloc(bse_ctx* ctx, bse_interp* s, int nvec, const 
     void* base = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_scratch_mu);
-        if (!g_scratch_addr[ctx->device]) {
-            void* p = nullptr;
-            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-            if (e != cudaSuccess || !p) {
-                ctx->err = std::string("cudaGetSymbolAddress of the static scratch failed: ") + cudaGetErrorString(e);
-                return BSE_ERR_CUDA;
-            }
-            g_scratch_addr[ctx->device] = p;
-        }
-        base = g_scratch_addr[ctx->device];
+        base = g_scratch_addr[ctx->device];           // looked up by bse_ctx_create
+    }
+    if (!base) {
+        ctx->err = "the static scratch of this device was not set up (bse_ctx_create)";
+        return BSE_ERR_CUDA;
     }
     // Carve the per-call buffers (each 256-byte aligned) out of the array.
     const bse_coarse* c = s->co;

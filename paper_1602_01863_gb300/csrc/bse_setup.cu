@@ -229,6 +229,37 @@ __global__ void k_build_kc(const double2* __restrict__ M, const double2* __restr
     }
 }
 
+// K_c given by the caller (complex128 [Nc][Nc]) converted to the storage precision.
+template <int PREC>
+__global__ void k_kc_from_user(const double2* __restrict__ user, int Nc, int ldk, void* __restrict__ out,
+                               __nv_bfloat16* __restrict__ kr, __nv_bfloat16* __restrict__ ki) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)Nc * Nc) return;
+    const double2 v = user[e];
+    const long long i = e / Nc, j = e % Nc;
+    if (PREC == BSE_PREC_F64) {
+        reinterpret_cast<double2*>(out)[e] = v;
+    } else if (PREC == BSE_PREC_F32) {
+        reinterpret_cast<float2*>(out)[e] = make_float2((float)v.x, (float)v.y);
+    } else {
+        kr[i * ldk + j] = __double2bfloat16(v.x);
+        ki[i * ldk + j] = __double2bfloat16(v.y);
+    }
+}
+
+// Dense table given by the caller (FP64 / complex128 host data copied to `tmp`)
+// into the vector precision.
+template <typename T>
+__global__ void k_real_to(const double* __restrict__ src, long long n, T* __restrict__ dst) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = (T)src[i];
+}
+template <typename V>
+__global__ void k_cplx_to(const double2* __restrict__ src, long long n, V* __restrict__ dst) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = from_d2<V>(src[i]);
+}
+
 // Dense tables, one thread per dense point kd:
 //   Delta E_vc(k) (exact on the dense mesh), dipoles P^alpha_vc(k) = [U_v^T pi^alpha conj(U_c)],
 //   and for all 8 corners d = U(k~)^H U(k) for both manifolds (Eq. completeness).
@@ -360,7 +391,7 @@ int bse_alloc(bse_ctx* ctx, void** p, size_t bytes, const char* what) {
         if (rc_ != BSE_OK) return rc_; \
     } while (0)
 
-int bse_setup_coarse_device(bse_ctx* ctx, bse_coarse* c) {
+int bse_setup_coarse_device(bse_ctx* ctx, bse_coarse* c, const void* user_kc) {
     const int n = c->n, nv = c->nv, nc = c->nc, nkc = c->nkc, Nc = c->Nc;
     cudaStream_t st = ctx->stream;
     TRY(bse_alloc(ctx, (void**)&c->d_Uv, sizeof(double2) * nkc * nv * nv, "coarse Uv"));
@@ -369,10 +400,12 @@ int bse_setup_coarse_device(bse_ctx* ctx, bse_coarse* c) {
     k_gauge<<<blocks_for(nkc, 64), 64, 0, st>>>(c->d_gen_c, nc, n, 1, nkc, c->d_Uc);
     double2* d_M = nullptr;
     double* d_h = nullptr;
-    TRY(bse_alloc(ctx, (void**)&d_M, sizeof(double2) * nkc * 26 * nv * nc, "form factors"));
-    TRY(bse_alloc(ctx, (void**)&d_h, sizeof(double) * nkc, "shape table"));
-    k_form_factors<<<blocks_for((long long)nkc * 26, 64), 64, 0, st>>>(c->d_Uv, c->d_Uc, c->d_mu, n, nv, nc, d_M);
-    k_shape_table<<<blocks_for(nkc, 128), 128, 0, st>>>(n, c->kappa, c->direct_shells, c->h_const, c->h0, 0, d_h);
+    if (!user_kc) {
+        TRY(bse_alloc(ctx, (void**)&d_M, sizeof(double2) * nkc * 26 * nv * nc, "form factors"));
+        TRY(bse_alloc(ctx, (void**)&d_h, sizeof(double) * nkc, "shape table"));
+        k_form_factors<<<blocks_for((long long)nkc * 26, 64), 64, 0, st>>>(c->d_Uv, c->d_Uc, c->d_mu, n, nv, nc, d_M);
+        k_shape_table<<<blocks_for(nkc, 128), 128, 0, st>>>(n, c->kappa, c->direct_shells, c->h_const, c->h0, 0, d_h);
+    }
     size_t bytes;
     if (c->kc_prec == BSE_PREC_F64) bytes = sizeof(double2) * (size_t)Nc * Nc;
     else if (c->kc_prec == BSE_PREC_F32) bytes = sizeof(float2) * (size_t)Nc * Nc;
@@ -386,7 +419,16 @@ int bse_setup_coarse_device(bse_ctx* ctx, bse_coarse* c) {
     }
     const double pref = c->e_k / nkc;
     dim3 bs(16, 16), gs(blocks_for(Nc, 16), blocks_for(Nc, 16));
-    if (c->kc_prec == BSE_PREC_F64)
+    if (user_kc) {
+        const long long ne = (long long)Nc * Nc;
+        const double2* u = static_cast<const double2*>(user_kc);
+        if (c->kc_prec == BSE_PREC_F64)
+            k_kc_from_user<BSE_PREC_F64><<<blocks_for(ne, 256), 256, 0, st>>>(u, Nc, c->ldk, c->d_kc, nullptr, nullptr);
+        else if (c->kc_prec == BSE_PREC_F32)
+            k_kc_from_user<BSE_PREC_F32><<<blocks_for(ne, 256), 256, 0, st>>>(u, Nc, c->ldk, c->d_kc, nullptr, nullptr);
+        else
+            k_kc_from_user<BSE_PREC_BF16><<<blocks_for(ne, 256), 256, 0, st>>>(u, Nc, c->ldk, nullptr, c->d_kr, c->d_ki);
+    } else if (c->kc_prec == BSE_PREC_F64)
         k_build_kc<BSE_PREC_F64><<<gs, bs, 0, st>>>(d_M, c->d_Uv, c->d_Uc, d_h, n, nv, nc, pref, 1.0 / c->eps_inf,
                                                    c->exchange_on, Nc, c->ldk, c->d_kc, nullptr, nullptr);
     else if (c->kc_prec == BSE_PREC_F32)
@@ -408,8 +450,44 @@ int bse_setup_coarse_device(bse_ctx* ctx, bse_coarse* c) {
 
 namespace {
 
+// Replace the model's dense tables by the caller's (bse_dense_inputs), after
+// k_dense_tables has written the model's.
 template <typename T>
-int setup_interp_typed(bse_ctx* ctx, bse_interp* s) {
+int apply_dense_inputs(bse_ctx* ctx, bse_interp* s, const bse_dense_inputs* in) {
+    using V = typename Cx<T>::V;
+    cudaStream_t st = ctx->stream;
+    const long long N = s->N, nDv = (long long)s->nk * 8 * s->nv * s->nv, nDc = (long long)s->nk * 8 * s->nc * s->nc;
+    const long long most = std::max(std::max(N, nDv), nDc);
+    double2* tmp = nullptr;
+    TRY(bse_alloc(ctx, (void**)&tmp, sizeof(double2) * (size_t)most, "dense input staging"));
+    cudaError_t e = cudaSuccess;
+    if (in->dE && e == cudaSuccess) {
+        e = cudaMemcpyAsync(tmp, in->dE, sizeof(double) * N, cudaMemcpyHostToDevice, st);
+        k_real_to<T><<<blocks_for(N, 256), 256, 0, st>>>((const double*)tmp, N, (T*)s->d_dE);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    if (in->P && e == cudaSuccess) e = cudaMemcpyAsync(s->d_P, in->P, sizeof(double2) * 3 * N, cudaMemcpyHostToDevice, st);
+    if (in->Dv && e == cudaSuccess) {
+        e = cudaMemcpyAsync(tmp, in->Dv, sizeof(double2) * nDv, cudaMemcpyHostToDevice, st);
+        k_cplx_to<V><<<blocks_for(nDv, 256), 256, 0, st>>>(tmp, nDv, (V*)s->d_Dv);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    if (in->Dc && e == cudaSuccess) {
+        e = cudaMemcpyAsync(tmp, in->Dc, sizeof(double2) * nDc, cudaMemcpyHostToDevice, st);
+        k_cplx_to<V><<<blocks_for(nDc, 256), 256, 0, st>>>(tmp, nDc, (V*)s->d_Dc);
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(tmp);
+    if (e != cudaSuccess) {
+        ctx->err = std::string("dense inputs: ") + cudaGetErrorString(e);
+        return BSE_ERR_CUDA;
+    }
+    return BSE_OK;
+}
+
+template <typename T>
+int setup_interp_typed(bse_ctx* ctx, bse_interp* s, const bse_dense_inputs* dense) {
     using V = typename Cx<T>::V;
     const bse_coarse* c = s->co;
     const int n = s->n, nd = s->nd, nk = s->nk, nv = s->nv, nc = s->nc, t = s->t, N = s->N;
@@ -435,6 +513,7 @@ int setup_interp_typed(bse_ctx* ctx, bse_interp* s) {
         ctx->err = std::string("dense set-up kernels: ") + cudaGetErrorString(e);
         return BSE_ERR_CUDA;
     }
+    if (dense) TRY(apply_dense_inputs<T>(ctx, s, dense));
     // scratch
     const size_t nvec = BSE_MAX_CHAINS;
     TRY(bse_alloc(ctx, &s->d_Q, sizeof(V) * nvec * c->Nc, "Q"));
@@ -570,7 +649,7 @@ int setup_interp_typed(bse_ctx* ctx, bse_interp* s) {
 
 }  // namespace
 
-int bse_setup_interp_device(bse_ctx* ctx, bse_interp* s) {
-    if (s->vec_prec == BSE_PREC_F64) return setup_interp_typed<double>(ctx, s);
-    return setup_interp_typed<float>(ctx, s);
+int bse_setup_interp_device(bse_ctx* ctx, bse_interp* s, const bse_dense_inputs* dense) {
+    if (s->vec_prec == BSE_PREC_F64) return setup_interp_typed<double>(ctx, s, dense);
+    return setup_interp_typed<float>(ctx, s, dense);
 }

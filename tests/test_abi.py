@@ -82,9 +82,11 @@ def test_null_arguments_are_rejected_on_the_host(built_lib):
     lldummy = (ctypes.c_longlong * 8)()
     calls = {
         "bse_ctx_create": lambda: lib.bse_ctx_create(N, 0, N),
-        "bse_build_coarse": lambda: lib.bse_build_coarse(N, N, 4, 0, N),
+        "bse_build_coarse": lambda: lib.bse_build_coarse(N, N, 4, 0, N, N),
         "bse_coarse_get_kc": lambda: lib.bse_coarse_get_kc(N, N, dummy),
-        "bse_interp_setup": lambda: lib.bse_interp_setup(N, N, 2, 0, ctypes.c_double(1.0), 0, N),
+        "bse_interp_setup": lambda: lib.bse_interp_setup(N, N, 2, 0, ctypes.c_double(1.0), 0, N, N),
+        "bse_set_stop_rule": lambda: lib.bse_set_stop_rule(N, ctypes.c_double(0.01), 10, ctypes.c_double(1.0),
+                                                           ctypes.c_double(0.1), 4, dummy),
         "bse_interp_info": lambda: lib.bse_interp_info(N, lldummy),
         "bse_dipoles": lambda: lib.bse_dipoles(N, N, 1, dummy, N, dummy),
         "bse_apply_h": lambda: lib.bse_apply_h(N, N, 1, N, N),

@@ -375,3 +375,27 @@ def test_m2_with_ndiv1_is_explicit():
     I = tiny_interp(n=3, nd=1, nv=2, nc=2, width=1.0)
     Hx, _ = om.explicit_dense_hamiltonian(I.model, 3, 1)
     assert np.abs(I.H_dense("m2") - Hx).max() < 1e-13
+
+
+# ------------------------------------------------- adaptive stop (Sec. 5.1)
+def test_converged_stop_rule():
+    """Sec. 5.1 stops a chain once the spectrum changes by less than 1 % (real
+    and imaginary parts).  The oracle's stop step must be a check point, the
+    change at it must be within the tolerance and the change at every earlier
+    check above it; the stopped spectrum must then be close to the exact one
+    (brute-force diagonalisation of the same H)."""
+    I = tiny_interp(n=4, nd=2, nv=2, nc=2, width=1.0)
+    H = I.H_dense("m3")
+    P = I.dipole([1, 0, 0])
+    w = synth.frequency_grid(500)
+    pref, eta, c, tol = 1.0 / I.Nk, 0.1, 5, 0.01
+    a, b, pn2, _ = oh.haydock_until_converged(lambda v: H @ v, P, 400, c, tol, pref, eta, w, "cgs2")
+    m = len(a)
+    assert m % c == 0 and 2 * c <= m < 400
+    changes = []
+    for j in range(c, m + 1, c):
+        changes.append(oh.epsilon(a[:j], b[:j + 1], pn2, pref, eta, w))
+    d = [max(oh.spectrum_change(changes[i], changes[i - 1])) for i in range(1, len(changes))]
+    assert d[-1] <= tol and all(x > tol for x in d[:-1])
+    exact = oh.epsilon_brute(H, P, pref, eta, w)
+    assert oh.spectrum_error(changes[-1].imag, exact.imag) < 5 * tol
