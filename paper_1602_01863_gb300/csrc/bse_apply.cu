@@ -15,6 +15,8 @@
 #include <cstring>
 #include <type_traits>
 
+#include <cuda_fp16.h>
+
 #include "bse_internal.cuh"
 
 namespace {
@@ -178,12 +180,14 @@ size_t restrict_st_smem(int nchains) {
 // Restrict (Eq. matmul1 gathered by Eq. ordersums), one CTA per target coarse
 // point k~: x(k, l) = f conj(Dv) psi Dc^T for every active pair of the source
 // cells k~ - l, written to X, and Q(k~) = sum of the x, summed over the 64 item
-// threads of each chain in a fixed order.
-template <int NV, int NC, bool OUT_BF16>
+// threads of each chain in a fixed order.  XH: X holds the pieces for the
+// tensor-core near field, FP16 (re, im) scaled by xscale[chain], t padded to a
+// multiple of 4 with zeros.
+template <int NV, int NC, bool OUT_BF16, bool XH>
 __global__ void __launch_bounds__(256) k_restrict_st(
     const float2* __restrict__ psi, const float2* __restrict__ Dv, const float2* __restrict__ Dc, int n, int nd,
     int nb1, int nchains, int N, int Nc, float2* __restrict__ Q, __nv_bfloat16* __restrict__ Bop, int ldk,
-    float2* __restrict__ X) {
+    void* __restrict__ X, const float* __restrict__ xscale) {
     constexpr int t = NV * NC, RV = NV * NV, RC = NC * NC;
     constexpr int RVp = odd_pad(RV), RCp = odd_pad(RC), TP = odd_pad(t);
     extern __shared__ float2 st_sm[];
@@ -271,16 +275,36 @@ __global__ void __launch_bounds__(256) k_restrict_st(
                 }
             }
             const size_t kd = (size_t)src_cell(l) * Ndiv + js;
-            float2* xo = X + (((size_t)c * nk + kd) * 8 + l) * t;
+            float2 xv[t];
 #pragma unroll
             for (int a = 0; a < NV; ++a)
 #pragma unroll
                 for (int bb = 0; bb < NC; ++bb) {
                     const float2 v = make_float2(x[a][bb].x * f, x[a][bb].y * f);
-                    if (X) xo[a * NC + bb] = v;
+                    xv[a * NC + bb] = v;
                     acc[a * NC + bb].x += v.x;
                     acc[a * NC + bb].y += v.y;
                 }
+            if constexpr (XH) {
+                constexpr int TPAD = (t + 3) & ~3;
+                const float sx = xscale[c];
+                uint4* xo = reinterpret_cast<uint4*>(reinterpret_cast<__half2*>(X) + (((size_t)c * nk + kd) * 8 + l) * TPAD);
+#pragma unroll
+                for (int q4 = 0; q4 < TPAD / 4; ++q4) {
+                    uint32_t w[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int e = 4 * q4 + u;
+                        const __half2 h = e < t ? __floats2half2_rn(xv[e].x * sx, xv[e].y * sx) : __floats2half2_rn(0.f, 0.f);
+                        w[u] = *reinterpret_cast<const uint32_t*>(&h);
+                    }
+                    xo[q4] = make_uint4(w[0], w[1], w[2], w[3]);
+                }
+            } else if (X) {
+                float2* xo = reinterpret_cast<float2*>(X) + (((size_t)c * nk + kd) * 8 + l) * t;
+#pragma unroll
+                for (int e = 0; e < t; ++e) xo[e] = xv[e];
+            }
         }
         __syncthreads();
     }
@@ -1312,10 +1336,47 @@ inline int dot_blocks(const bse_interp* s) {
     return vec_blocks(s->N);
 }
 
+// FP32 pieces (X32, [chain][nk][8][t]) -> FP16 pieces for the tensor-core near
+// field ([chain][nk][8][tpad], scaled by xscale[chain], zero padding).
+__global__ void __launch_bounds__(256) k_pieces_to_half(const float2* __restrict__ X32, int nk, int t, int tpad,
+                                                        int nchains, const float* __restrict__ xscale,
+                                                        __half2* __restrict__ Xh) {
+    const long long n = (long long)nchains * nk * 8 * tpad;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long piece = i / tpad;
+        const int e = (int)(i - piece * tpad), ch = (int)(piece / ((long long)nk * 8));
+        const float sx = xscale[ch];
+        const float2 v = e < t ? X32[piece * t + e] : make_float2(0.f, 0.f);
+        Xh[i] = __floats2half2_rn(v.x * sx, v.y * sx);
+    }
+}
+
+// FP16 piece scale per chain from the input's 2-norm (bse_near_tc_xscale on
+// the device): the largest power of two with scale dbound ||psi|| <= 2^15.
+__global__ void __launch_bounds__(256) k_chain_xscale(const float2* __restrict__ psi, int N, double dbound,
+                                                      float* __restrict__ xscale) {
+    __shared__ double2 sh[256];
+    const int ch = blockIdx.x;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const float2 v = psi[(size_t)ch * N + i];
+        s += (double)v.x * v.x + (double)v.y * v.y;
+    }
+    const double2 r = block_sum2(make_double2(s, 0.0), sh);
+    if (threadIdx.x == 0) {
+        const double b = fmax(dbound * fmax(sqrt(r.x), 1e-300), 1e-300);
+        int e = 0;
+        frexp(32768.0 / b, &e);
+        xscale[ch] = (float)ldexp(1.0, e - 1);
+    }
+}
+
 // Restrict: staged FP32 kernel for 3x3, 4x4 and 4x6 bands (N_div <= 64), generic otherwise.
+// xh: the pieces go to X as FP16 for the tensor-core near field (scaled by
+// xscale); the generic kernel then writes FP32 pieces to x32 first.
 template <typename T>
 void launch_restrict(bse_ctx* ctx, const bse_interp* s, int nchains, const void* psi, void* Q, __nv_bfloat16* bop,
-                     void* X) {
+                     void* X, bool xh, const float* xscale, void* x32) {
     using V = typename Cx<T>::V;
     const bse_coarse* c = s->co;
     cudaStream_t st = ctx->stream;
@@ -1324,34 +1385,42 @@ void launch_restrict(bse_ctx* ctx, const bse_interp* s, int nchains, const void*
         const float2* p = (const float2*)psi;
         const float2* dv = (const float2*)s->d_Dv;
         const float2* dc = (const float2*)s->d_Dc;
+#define BSE_ST_RESTRICT_V(NV_, NC_, BF_, XH_)                                                                       \
+    {                                                                                                               \
+        const size_t smem = restrict_st_smem<NV_, NC_>(nchains);                                                    \
+        ensure_smem(k_restrict_st<NV_, NC_, BF_, XH_>, smem);                                                       \
+        k_restrict_st<NV_, NC_, BF_, XH_><<<c->nkc, 256, smem, st>>>(p, dv, dc, s->n, s->nd, s->nb1, nchains, s->N, \
+                                                                    c->Nc, BF_ ? nullptr : (float2*)Q, BF_ ? bop : nullptr, \
+                                                                    BF_ ? c->ldk : 0, X, xscale);                   \
+    }
 #define BSE_ST_RESTRICT(NV_, NC_)                                                                                   \
     if (s->nv == NV_ && s->nc == NC_ && s->Ndiv <= 64) {                                                            \
-        const size_t smem = restrict_st_smem<NV_, NC_>(nchains);                                                    \
-        if (bf) {                                                                                                   \
-            ensure_smem(k_restrict_st<NV_, NC_, true>, smem);                                                       \
-            k_restrict_st<NV_, NC_, true><<<c->nkc, 256, smem, st>>>(p, dv, dc, s->n, s->nd, s->nb1, nchains, s->N,\
-                                                                    c->Nc, nullptr, bop, c->ldk, (float2*)X);       \
-        } else {                                                                                                    \
-            ensure_smem(k_restrict_st<NV_, NC_, false>, smem);                                                      \
-            k_restrict_st<NV_, NC_, false><<<c->nkc, 256, smem, st>>>(p, dv, dc, s->n, s->nd, s->nb1, nchains,     \
-                                                                     s->N, c->Nc, (float2*)Q, nullptr, 0,           \
-                                                                     (float2*)X);                                   \
-        }                                                                                                           \
+        if (bf && xh) BSE_ST_RESTRICT_V(NV_, NC_, true, true)                                                       \
+        else if (bf) BSE_ST_RESTRICT_V(NV_, NC_, true, false)                                                       \
+        else if (xh) BSE_ST_RESTRICT_V(NV_, NC_, false, true)                                                       \
+        else BSE_ST_RESTRICT_V(NV_, NC_, false, false)                                                              \
         return;                                                                                                     \
     }
         BSE_ST_RESTRICT(3, 3)
         BSE_ST_RESTRICT(4, 4)
         BSE_ST_RESTRICT(4, 6)
 #undef BSE_ST_RESTRICT
+#undef BSE_ST_RESTRICT_V
     }
+    void* xout = xh ? x32 : X;
     if (bf)
         k_restrict<T, true><<<c->nkc, 256, 0, st>>>((const V*)psi, (const V*)s->d_Dv, (const V*)s->d_Dc, s->n, s->nd,
                                                    s->nv, s->nc, s->nb1, nchains, s->N, c->Nc, nullptr, bop, c->ldk,
-                                                   (V*)X, nullptr);
+                                                   (V*)xout, nullptr);
     else
         k_restrict<T, false><<<c->nkc, 256, 0, st>>>((const V*)psi, (const V*)s->d_Dv, (const V*)s->d_Dc, s->n, s->nd,
                                                     s->nv, s->nc, s->nb1, nchains, s->N, c->Nc, (V*)Q, nullptr, 0,
-                                                    (V*)X, nullptr);
+                                                    (V*)xout, nullptr);
+    if (xh) {
+        const long long n = (long long)nchains * s->nk * 8 * s->nf_tc_tpad;
+        const int g = (int)std::min<long long>((n + 255) / 256, 4096);
+        k_pieces_to_half<<<g, 256, 0, st>>>((const float2*)x32, s->nk, s->t, s->nf_tc_tpad, nchains, xscale, (__half2*)X);
+    }
 }
 
 // Prolong + diagonal: staged FP32 kernel for 3x3, 4x4 and 4x6 bands (N_div <= 64), generic otherwise.
@@ -1425,18 +1494,29 @@ struct Timer {
 
 // One application of H to nchains vectors psi -> w (device, vector precision),
 // block partials of <psi, w> into s->d_part_dot.
+// The tensor-core near field serves this application (FP16 pieces from restrict).
+inline bool near_tc_active(const bse_interp* s) {
+    return s->scheme == BSE_SCHEME_M3 && s->nf_tc && !s->nf_force_cuda_cores;
+}
+
+// unit: every psi has 2-norm 1 (the Lanczos vectors), so the FP16 piece scale
+// set up for unit vectors applies; otherwise it is computed from the norms.
 template <typename T>
-int apply_h_typed(bse_ctx* ctx, bse_interp* s, int nchains, const void* psi_v, void* w_v, bool prof) {
+int apply_h_typed(bse_ctx* ctx, bse_interp* s, int nchains, const void* psi_v, void* w_v, bool prof, bool unit) {
     using V = typename Cx<T>::V;
     const bse_coarse* c = s->co;
     cudaStream_t st = ctx->stream;
     const V* psi = (const V*)psi_v;
     V* W = (V*)w_v;
     const bool m3 = s->scheme == BSE_SCHEME_M3;
-    V* X = m3 ? (V*)s->d_X : nullptr;
+    const bool xh = near_tc_active(s);
+    void* X = m3 ? s->d_X : nullptr;
+    const float* xscale = unit ? s->d_xscale : s->d_xscale_gen;
+    if (xh && !unit)
+        k_chain_xscale<<<nchains, 256, 0, st>>>((const float2*)psi, s->N, s->dbound, s->d_xscale_gen);
     {
         Timer tm(ctx, prof, KC_RESTRICT);
-        launch_restrict<T>(ctx, s, nchains, psi, s->d_Q, s->d_Bop, X);
+        launch_restrict<T>(ctx, s, nchains, psi, s->d_Q, s->d_Bop, X, xh, xscale, s->d_U);
     }
     {
         Timer tm(ctx, prof, KC_KCAPPLY);
@@ -1449,7 +1529,7 @@ int apply_h_typed(bse_ctx* ctx, bse_interp* s, int nchains, const void* psi_v, v
     }
     if (m3) {
         Timer tm(ctx, prof, KC_NEAR);
-        int rc = bse_launch_near_field(ctx, s, nchains, X, s->d_U);
+        int rc = bse_launch_near_field(ctx, s, nchains, X, xscale, s->d_U);
         if (rc != BSE_OK) return rc;
     }
     {
@@ -1610,7 +1690,7 @@ int enqueue_chains(bse_ctx* ctx, bse_interp* s, int nch, int m, bool reorth, boo
     k_start_norm<T><<<nch, 256, 0, st>>>(s->d_part_nrm, nb, m, s->d_pn2, s->d_b);
     k_start_scale<T><<<nb, BSE_VEC_THREADS, 0, st>>>(B, s->d_pn2, N, nch, A, basis, mb);
     for (int i = 0; i < m; ++i) {
-        int rc = apply_h_typed<T>(ctx, s, nch, B, W, prof);
+        int rc = apply_h_typed<T>(ctx, s, nch, B, W, prof, true);
         if (rc != BSE_OK) return rc;
         Timer tm(ctx, prof, KC_LANCZOS);
         k_reduce_a<<<nch, 256, 0, st>>>(s->d_part_dot, dot_blocks(s), i, m, s->d_a, s->d_aim, s->d_stop);
@@ -1786,8 +1866,8 @@ void bse_release_ctx_state(bse_ctx* ctx) {
 void bse_invalidate_graph(bse_interp* s) { drop_graph(s); }
 
 int bse_apply_once(bse_ctx* ctx, bse_interp* s, int nvec, const void* x, void* y, bool profile) {
-    int rc = (s->vec_prec == BSE_PREC_F64) ? apply_h_typed<double>(ctx, s, nvec, x, y, profile)
-                                           : apply_h_typed<float>(ctx, s, nvec, x, y, profile);
+    int rc = (s->vec_prec == BSE_PREC_F64) ? apply_h_typed<double>(ctx, s, nvec, x, y, profile, false)
+                                           : apply_h_typed<float>(ctx, s, nvec, x, y, profile, false);
     if (rc != BSE_OK) return rc;
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e == cudaSuccess) e = cudaGetLastError();
@@ -1963,18 +2043,20 @@ int apply_scratch_typed(bse_ctx* ctx, const bse_interp* s, int nchains, const vo
     const V* psi = (const V*)psi_v;
     V* W = (V*)w_v;
     const bool m3 = s->scheme == BSE_SCHEME_M3;
-    V* X = m3 ? (V*)sc.X : nullptr;
+    const bool xh = near_tc_active(s);
+    void* X = m3 ? sc.X : nullptr;
+    if (xh) k_chain_xscale<<<nchains, 256, 0, st>>>((const float2*)psi, s->N, s->dbound, s->d_xscale_gen);
     if (c->kc_prec == BSE_PREC_BF16) {
         BSE_CUDA_TRY(ctx, cudaMemsetAsync(sc.bop, 0, sizeof(__nv_bfloat16) * 16 * (size_t)c->ldk, st));
-        launch_restrict<T>(ctx, s, nchains, psi, nullptr, sc.bop, X);
+        launch_restrict<T>(ctx, s, nchains, psi, nullptr, sc.bop, X, xh, s->d_xscale_gen, sc.U);
         int rc = bse_tc_apply_scratch(ctx, s, nchains, sc.bop, sc.part, sc.R);
         if (rc != BSE_OK) return rc;
     } else {
-        launch_restrict<T>(ctx, s, nchains, psi, sc.Q, nullptr, X);
+        launch_restrict<T>(ctx, s, nchains, psi, sc.Q, nullptr, X, xh, s->d_xscale_gen, sc.U);
         k_kc_apply_simt<T><<<(c->Nc + 7) / 8, 256, 0, st>>>((const V*)c->d_kc, (const V*)sc.Q, c->Nc, nchains, (V*)sc.R);
     }
     if (m3) {
-        int rc = bse_launch_near_field(ctx, s, nchains, X, sc.U);
+        int rc = bse_launch_near_field(ctx, s, nchains, X, s->d_xscale_gen, sc.U);
         if (rc != BSE_OK) return rc;
     }
     launch_prolong<T>(ctx, s, nchains, sc.R, m3 ? sc.U : nullptr, psi, W, sc.dot);
@@ -2020,10 +2102,10 @@ int launch_near_rb(bse_ctx* ctx, const bse_interp* s, int nchains, const void* X
 }
 
 template <typename T>
-int launch_near_typed(bse_ctx* ctx, const bse_interp* s, int nchains, const void* X, void* U) {
+int launch_near_typed(bse_ctx* ctx, const bse_interp* s, int nchains, const void* X, const float* xscale, void* U) {
     using V = typename Cx<T>::V;
     if constexpr (std::is_same<T, float>::value) {
-        if (s->nf_tc && !s->nf_force_cuda_cores) return bse_near_tc_launch(ctx, s, nchains, X, U);
+        if (near_tc_active(s)) return bse_near_tc_launch(ctx, s, nchains, X, xscale, U);
         if (s->cell_smem && s->npairs <= 512) {
             // rows of the slot staging each of the 512 threads owns
             const int rows = (s->npairs + 512 / s->t - 1) / (512 / s->t);
@@ -2053,7 +2135,7 @@ int launch_near_typed(bse_ctx* ctx, const bse_interp* s, int nchains, const void
 }  // namespace
 
 // M3 near field for nchains chains: X pieces in, u pieces out (both [chain][nk][8][t]).
-int bse_launch_near_field(bse_ctx* ctx, const bse_interp* s, int nchains, const void* X, void* U) {
-    return (s->vec_prec == BSE_PREC_F64) ? launch_near_typed<double>(ctx, s, nchains, X, U)
-                                         : launch_near_typed<float>(ctx, s, nchains, X, U);
+int bse_launch_near_field(bse_ctx* ctx, const bse_interp* s, int nchains, const void* X, const float* xscale, void* U) {
+    return (s->vec_prec == BSE_PREC_F64) ? launch_near_typed<double>(ctx, s, nchains, X, xscale, U)
+                                         : launch_near_typed<float>(ctx, s, nchains, X, xscale, U);
 }

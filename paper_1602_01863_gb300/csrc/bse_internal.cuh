@@ -169,6 +169,11 @@ struct bse_interp {
     int* d_cstart = nullptr;         // [Ndiv][nslot + 1]
     size_t cell_smem = 0;            // dynamic shared memory of the cell kernel (0: not usable)
     int nf_tc = 0;                   // the tensor-core near field serves this handle
+    int nf_tc_tpad = 0;              // FP16 pieces per (dense k, corner): t rounded up to a multiple of 4
+    float nf_tc_sb = 1.f;            // stage-2 operand scale (power of two)
+    double dbound = 0;               // bound of ||d_v||_F ||d_c||_F over the non-zero-weight pieces
+    float* d_xscale = nullptr;       // [4] FP16 piece scales of unit-norm vectors (Haydock loop)
+    float* d_xscale_gen = nullptr;   // [4] piece scales computed from the input norms (bse_apply_h)
     int nf_tc_nsl = 0;               // slots that reach the cell
     int nf_tc_nkg = 0;               // their stage-1 K-blocks
     int nf_tc_nrows = 0;             // their source rows (all slots)
@@ -283,10 +288,11 @@ struct ApplyScratch {
     __nv_bfloat16* bop;      // [16][ldk]          (BF16 path only)
     float* part;             // tile partials      (BF16 path only)
 };
-int bse_launch_near_field(bse_ctx* ctx, const bse_interp* s, int nchains, const void* X, void* U);
+int bse_launch_near_field(bse_ctx* ctx, const bse_interp* s, int nchains, const void* X, const float* xscale, void* U);
 int bse_apply_learned(bse_ctx* ctx, const bse_interp* s, int nchains, const void* psi, void* w, double2* dot);
 int bse_near_tc_prepare(bse_ctx* ctx, bse_interp* s, const std::vector<std::vector<NearEntry>>& per_slot);
-int bse_near_tc_launch(bse_ctx* ctx, const bse_interp* s, int nchains, const void* X, void* U);
+int bse_near_tc_launch(bse_ctx* ctx, const bse_interp* s, int nchains, const void* Xh, const float* xscale, void* U);
+float bse_near_tc_xscale(const bse_interp* s, double norm);
 size_t bse_tc_part_bytes(const bse_interp* s);
 int bse_tc_apply_scratch(bse_ctx* ctx, const bse_interp* s, int nchains, __nv_bfloat16* bop, float* part, void* R);
 int bse_apply_scratch(bse_ctx* ctx, const bse_interp* s, int nvec, const void* x, void* y, const ApplyScratch& sc);

@@ -1,99 +1,105 @@
-// Method 3 near field on the tensor cores, as two chained GEMMs per coarse cell.
+// Method 3 near field on the tensor cores: two chained GEMMs per coarse cell,
+// FP16 operands (10 explicit mantissa bits, as TF32) with power-of-two scales,
+// FP32 accumulation in TMEM.
 //
 // For one coarse cell C, one Lanczos step and every chain, the correction in
 // coarse-basis form is
 //   u(k, l) = sum_s A(k~_l, k~_s) [y1(k, s) - h_head(q_c(l, s)) z(k, s)],
 //   y1(k, s) = sum_{k' near k, k' in slot s} h_head(q_d(k, k')) x(k'),   z(k, s) = sum x(k'),
 // A = alpha O^v (x) O^c the Kronecker head block of Eq. diverg, s over the
-// source slots, k over the N_div targets of C.
+// source slots (coarse points), k over the N_div targets of C, x(k') the
+// restricted pieces of Eq. matmul1.
 // Stage 1 (per slot): y1 and z are a product of the slot's near pattern S_s
 // (rows (y1|z, target), columns = the slot's source rows; entries h_head(q_d)
 // or 1) with the gathered source rows X_s.  S_s is the same for every cell
 // (translation invariance of the near pattern), so set-up writes it once as
-// TF32 images of 32-row K-blocks; the kernel gathers X_s (all chains, columns
-// (chain, e, re|im)) transposed into shared memory and issues
-//   D1 [128 = (y1|z, target)] x [32 * chains] += S_s[., K-block] * X_s[K-block]^T.
-// Stage 2 (per slot): D1 is read back from TMEM into the B operand
-//   B_s[(chain, k), (Y|Z, e', re|im)]  = y1(k, s), z(k, s)
-// and, with the real form
-//   Ahat_s[(l,e,.), (Y,e',.)] = [[Re c, -Im c], [Im c, Re c]],  c = A(k~_l, k~_s)[e][e'],
+// FP16 images of 32-row K-blocks (K-major, 64-byte swizzle).  The source rows
+// are FP16 pieces s_x x (restrict writes them with a per-chain power-of-two
+// scale s_x, padded to a multiple of 4 transitions), gathered by 16-byte
+// cp.async into an MN-major operand (one 64-byte row per source row and chain):
+//   D1 [128 = (y1|z, target)] x [32 * chains] += S_s[., K-block] * X_s[K-block].
+// Stage 2 (per slot): the converters read D1 back from TMEM, scale it by s_b
+// and write the K-major FP16 operand
+//   B_s[(chain, k), (Y|Z, e', re|im)] = s_b s_x y1(k, s), s_b s_x z(k, s);
+// the head writers form, from the per-cell head factors,
+//   Ahat_s[(l,e,.), (Y,e',.)] = [[Re c, -Im c], [Im c, Re c]],  c = A(k~_l, k~_s)[e][e'] / alpha,
 //   Ahat_s[(l,e,.), (Z,e',.)] = the same for -h_head(q_c(l, s)) c,
-// formed in shared memory from the per-cell head factors,
+// and the issuer accumulates
 //   D2 [256 = (l, e, re|im)] x [64 * chains] += Ahat_s [256 x 64] * B_s^T.
-// tcgen05.mma kind::tf32 (10-bit mantissa, FP32 range: y1 and h_head z nearly
-// cancel in u, which BF16 would not resolve), FP32 accumulators in TMEM.
+// The epilogue writes u = alpha D2 / (s_x s_b).  The scales keep every FP16
+// operand inside its normal range: |x s_x| <= 2^15 from the bound
+// |x| <= ||d_v||_F ||d_c||_F ||psi||_2, and |y1 s_x s_b|, |z s_x s_b| <= 2^15 from
+// |y1| <= h_max sqrt(n_near) ||x||_2; c / 1 and h_head c are at most h_max.
 //
-// Warp roles (768 threads, one CTA per coarse cell):
-//   warps 4-7      MMA issuer (warp 4, lane 0, also TMEM owner) and D1 -> B
-//                  converters (TMEM lane quarters 0-3); after each slot the four
-//                  warps convert D1 and meet at a named barrier, after which the
-//                  issuer goes on.  Waits use the blocking mbarrier test: a
-//                  spinning issuer measurably slowed the other warps
-//   warps 8-15     stage-1 producers: the S image by one bulk copy, the X rows by
-//                  4-byte cp.async gathers laid out so that a warp's 32 stores
-//                  hit 32 distinct banks; each warp keeps the whole ring in
-//                  flight and signals a stage once its copies have landed
-//   warps 0-3, 16-23  Ahat writers (per slot, in two 128-row halves), with the
-//                  slot's head factors staged one slot ahead
-// The stage-2 MMAs of slot i - 1 are issued between the stage-1 K-blocks of slot
-// i, so the tensor pipe works on one while the producers refill the ring; D1 and
-// B are single-buffered (TMEM holds D2, 2 x 64 x chains columns, and D1,
-// 32 x chains), Ahat is released half by half.
-// Constraints: t <= 16, N_div <= 64, FP32 vectors, <= 3 chains per launch.
+// Warp roles (512 threads, one CTA per coarse cell):
+//   warp 0         MMA issuer (lane 0) and TMEM owner
+//   warps 4-7      converters (TMEM lane quarter = warp % 4)
+//   warps 8-11     producers: per K-block one thread issues the S-image bulk
+//                  copy, every thread 16-byte cp.async gathers of X rows, and
+//                  cp.async.mbarrier.arrive signals the stage when they land
+//   warps 1-3, 12-15  head writers (Ahat), head factors staged one slot ahead
+// Pipeline: a 6-stage ring for stage 1; D1 single (TMEM), B and Ahat double
+// buffered (shared memory), so the converters and head writers of slot i work
+// while the tensor cores run stage 2 of slot i - 1 and stage 1 of slot i + 1.
+// Constraints: 2 <= t <= 16, N_div <= 64, FP32 vectors, <= 3 chains per launch.
 // Every wait is bounded; on expiry the kernel raises bit 1 of the status word,
-// every role leaves its loop, the MMAs and copies in flight are drained and
+// every role leaves its loop, the copies and MMAs in flight are drained and
 // TMEM is freed.
 #include <cuda.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
+#include <cmath>
 #include <functional>
 
 #include "bse_internal.cuh"
 
 namespace {
 
-constexpr int NT_M = 256;                    // rows (corner l, transition e, re|im), 8 * 16 * 2
-constexpr int NT_N = 64;                     // targets of the cell (padded)
+constexpr int NT_THREADS = 512;
 constexpr int NT_KB = 32;                    // source rows per stage-1 K-block
-constexpr int NT_STAGES = 3;                 // stage-1 ring depth
-constexpr int S_BYTES = 128 * NT_KB * 4;     // one S image K-block: 16 KB
-constexpr int A_KB = NT_M * 128;             // one 32-element K-block of A: 32 KB
-constexpr int A_BYTES = 2 * A_KB;            // 64 KB per slot
-constexpr int NT_THREADS = 768;
+constexpr int NT_STAGES = 6;                 // stage-1 ring depth
+constexpr int S_BYTES = 128 * NT_KB * 2;     // one S image K-block: 8 KB (FP16, K-major, 64 B rows)
+constexpr int XB_BYTES = NT_KB * 64;         // X tile per chain: 32 rows x 64 B (MN-major, 64-byte swizzle)
+constexpr int A_BYTES = 256 * 128;           // Ahat: 256 rows x 64 FP16 (128 B) = 32 KB
 constexpr int NT_TMEM_COLS = 512;
-constexpr int W_C0 = 4, W_CN = 4;            // MMA issuer (warp 4, lane 0) + converters (warp % 4 = TMEM lane quarter)
-constexpr int W_P0 = 8, W_PN = 8;            // producers: warp W_P0 + p stages rows 4p .. 4p + 3
-constexpr int W_A1 = 16;                     // Ahat writers: warps 0-3 and 16-23
-constexpr int W_AN = W_C0 + (NT_THREADS / 32 - W_A1);
-constexpr int NT_A = 32 * W_AN;              // Ahat writer threads
-constexpr int NT_AMAX = 3;                   // items per writer thread and slot (8 t ceil(t / 2) <= 1024)
-static_assert(NT_A * NT_AMAX >= 1024, "Ahat items per slot");
+constexpr int W_ISS = 0;                     // MMA issuer
+constexpr int W_CV0 = 4;                     // converters: warps 4-7
+constexpr int W_P0 = 8, W_PN = 4;            // producers: warps 8-11
+constexpr int NT_P = 32 * W_PN;              // producer threads
+constexpr int NT_AW = 7;                     // head writers: warps 1-3, 12-15
+constexpr int NT_A = 32 * NT_AW;
 constexpr long long NT_WAIT_CYCLES = 400000000LL;   // ~0.2 s; a whole launch takes well under 10 ms
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(su32(dst)), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(su32(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-// every group but the newest NT_STAGES - 1 landed (the K-block NT_STAGES - 1 behind the newest)
-__device__ __forceinline__ void cp_async_wait_lag() { asm volatile("cp.async.wait_group %0;" ::"n"(NT_STAGES - 1) : "memory"); }
+__device__ __forceinline__ void cp_async_arrive_noinc(uint32_t bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ uint32_t f2tf32(float v) {
-    uint32_t u;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(v));
-    return u;
-}
 
-// Byte offset of 32-bit element (row r, column k) of a K-major operand stored as
-// K-blocks of 32 elements (128-byte rows), each block `rows` x 128 B with the
-// 128-byte swizzle: 8-row atoms of 1024 B, 16-byte chunks XORed by r % 8.
-__host__ __device__ __forceinline__ uint32_t sw128(int r, int k, int rows) {
-    const int kb = k >> 5, kk = k & 31;
-    return (uint32_t)(kb * rows * 128 + (r >> 3) * 1024 + (r & 7) * 128 + ((((kk >> 2) ^ (r & 7)) & 7) << 4) + ((kk & 3) << 2));
+// Byte offset of a 16-byte chunk in a K-major operand of 128-byte rows with
+// the 128-byte swizzle (8-row atoms of 1024 B, chunk XOR row % 8).
+__host__ __device__ __forceinline__ uint32_t sw128(int r, int chunk) {
+    return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + (((chunk ^ r) & 7) << 4));
+}
+// Byte offset of FP16 element (row r, k) in a K-major operand of 64-byte rows
+// with the 64-byte swizzle (8-row atoms of 512 B, chunk XOR (row / 2) % 4).
+__host__ __device__ __forceinline__ uint32_t sw64(int r, int k) {
+    return (uint32_t)((r >> 3) * 512 + (r & 7) * 64 + ((((k >> 3) ^ (r >> 1)) & 3) << 4) + (k & 7) * 2);
 }
 
 __device__ __forceinline__ void bar_init(uint32_t b, uint32_t c) {
@@ -111,15 +117,8 @@ __device__ __forceinline__ bool bar_try(uint32_t b, uint32_t parity) {
                  : "=r"(ok) : "r"(b), "r"(parity) : "memory");
     return ok != 0;
 }
-// Non-blocking test of a phase.
-__device__ __forceinline__ bool bar_test(uint32_t b, uint32_t parity) {
-    uint32_t ok;
-    asm volatile("{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-                 : "=r"(ok) : "r"(b), "r"(parity) : "memory");
-    return ok != 0;
-}
 // Bounded wait: false when another role gave up (abort flag) or the clock
-// budget ran out (raises status bit 1 and the abort flag).
+// budget ran out (raises status bit 2 and the abort flag).
 __device__ __forceinline__ bool bar_wait(uint32_t b, uint32_t parity, int* status, volatile int* abort_flag) {
     const long long t0 = clock64();
     while (!bar_try(b, parity)) {
@@ -143,16 +142,19 @@ __device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                  ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
 }
-__device__ __forceinline__ uint64_t desc_sw128(uint32_t addr) {
-    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+// Shared-memory matrix descriptors (tcgen05): start, leading / stride byte
+// offsets (16-byte units), version 1, swizzle mode (2: 128 B, 4: 64 B).
+__device__ __forceinline__ uint64_t make_desc(uint32_t addr, uint32_t lbo, uint32_t sbo, uint32_t mode) {
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)mode << 61);
 }
-// kind::tf32, A = B = TF32, D = F32, both K-major, M = 128, N as given
-__host__ __device__ constexpr uint32_t idesc_tf32(int N) {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+// kind::f16 instruction descriptor: A = B = FP16, D = F32, A K-major, B K- or
+// MN-major, M = 128, N as given.
+__host__ __device__ constexpr uint32_t idesc_f16(int N, bool b_mn_major) {
+    return (1u << 4) | ((b_mn_major ? 1u : 0u) << 16) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
 __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
                  ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 __device__ __forceinline__ void commit(uint32_t b) {
@@ -169,15 +171,16 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
           "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void writers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(NT_A) : "memory"); }
-__device__ __forceinline__ void converters_sync() { asm volatile("bar.sync 2, %0;" ::"n"(32 * W_CN) : "memory"); }
-__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(su32(dst)), "l"(src) : "memory");
+
+__device__ __forceinline__ uint32_t pack_h2(float a, float b) {
+    const __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
 }
 
 // Shared-memory bytes of one head-factor buffer: Hv, Hc of the 8 target corners
@@ -186,43 +189,36 @@ __host__ __device__ __forceinline__ int hb_bytes(int nv, int nc) {
     return ((8 * (nv * nv + nc * nc) * 8 + 32) + 15) & ~15;
 }
 
-// Pack four values rounded to TF32 into one 16-byte chunk.
-__device__ __forceinline__ uint4 pack_tf32(float a, float b, float c, float d) {
-    return make_uint4(f2tf32(a), f2tf32(b), f2tf32(c), f2tf32(d));
-}
-
 // Shared-memory layout (bytes from the 1024-aligned base) for `nch` chains.
 struct NtLayout {
     int N1, N2, b_off, ring_off, stage_bytes, tab_off;
     __host__ __device__ NtLayout(int nch) {
         N1 = 32 * nch;
         N2 = 64 * nch;
-        b_off = A_BYTES;                                  // Ahat: [2 K-blocks][256 rows][128 B]
-        ring_off = b_off + 2 * N2 * 128;                  // B: [2 K-blocks (Y, Z)][N2 rows][128 B]
-        stage_bytes = S_BYTES + N1 * 128;                 // ring stage: S K-block | X K-block
+        b_off = 2 * A_BYTES;                              // Ahat: [2 buffers][256 rows][128 B]
+        ring_off = b_off + 2 * N2 * 128;                  // B: [2 buffers][N2 rows][128 B]
+        stage_bytes = S_BYTES + nch * XB_BYTES;           // ring stage: S K-block | X tile per chain
         tab_off = ring_off + NT_STAGES * stage_bytes;     // head-factor buffers [2], then slot tables
     }
 };
 
-// Slot table entry {slot, first K-block, K-blocks, source rows} and per-K-block
-// info (slot ordinal | K-block in slot << 16) are staged in shared memory.
 __global__ void __launch_bounds__(NT_THREADS, 1) k_near_tc(
-    const float* __restrict__ X, const int* __restrict__ rows, const int4* __restrict__ slots,
-    const int* __restrict__ rowstart, const int* __restrict__ kinfo, int nsl, int nkg, int nrows,
+    const __half2* __restrict__ X, int tpad, const int* __restrict__ rows, const int4* __restrict__ slots,
+    const int* __restrict__ rowstart, const int* __restrict__ kinfo, int nsl, int nkg,
     const unsigned char* __restrict__ Simg, const float2* __restrict__ Hv, const float2* __restrict__ Hc,
     const float* __restrict__ hc, int n, int nd, int nv, int nc, int nb1, int smin, int ns1, int rmin, int nr1,
-    int nch, float2* __restrict__ U, int* __restrict__ status) {
+    int nch, const float* __restrict__ xscale, float sb, float alpha, float2* __restrict__ U, int* __restrict__ status) {
     // an earlier launch on this context gave up a wait: skip (the host reports BSE_ERR_TIMEOUT)
     if (*reinterpret_cast<volatile int*>(status) & 2) return;
     extern __shared__ unsigned char raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~(uintptr_t)1023);
-    __shared__ uint64_t bar_full[NT_STAGES], bar_sfull[NT_STAGES], bar_empty[NT_STAGES];
-    __shared__ uint64_t bar_d1_full, bar_a_full[2], bar_a_free[2], bar_d2;
+    __shared__ uint64_t bar_full[NT_STAGES], bar_empty[NT_STAGES];
+    __shared__ uint64_t bar_d1_full, bar_d1_free, bar_b_full[2], bar_b_free[2], bar_a_full[2], bar_a_free[2], bar_d2;
     __shared__ uint32_t tmem_sh;
     __shared__ int abort_sh;
     volatile int* abort_flag = &abort_sh;
     const int t = nv * nc, Ndiv = nd * nd * nd, nslot = ns1 * ns1 * ns1, nrel = nr1 * nr1 * nr1;
-    const int nk = n * n * n * Ndiv, th = (t + 1) >> 1;
+    const int nk = n * n * n * Ndiv;
     // D2 rows (l, e, re|im) = 2 (l t + e) + re|im; the second 128-row half holds
     // anything only when 16 t > 128
     const int nmh = (16 * t > 128) ? 2 : 1;
@@ -238,14 +234,9 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_near_tc(
     int* s_rs = reinterpret_cast<int*>(s_sl + nsl);             // [nsl]
     int* s_ki = s_rs + nsl;                                     // [nkg]
     int* scell = s_ki + nkg;                                    // [nslot][8] source cells
-    unsigned short* s_rows = reinterpret_cast<unsigned short*>(scell + nslot * 8);   // [nrows] js | corner << 8
     const Int3 ci = unflat3(cell, n);
     for (int i = tid; i < nsl; i += NT_THREADS) { s_sl[i] = slots[i]; s_rs[i] = rowstart[i]; }
     for (int i = tid; i < nkg; i += NT_THREADS) s_ki[i] = kinfo[i];
-    for (int i = tid; i < nrows; i += NT_THREADS) {
-        const int code = rows[i];
-        s_rows[i] = (unsigned short)((code & 0xFF) | ((code >> 16) << 8));
-    }
     for (int i = tid; i < nslot * 8; i += NT_THREADS) {
         const int s = i >> 3, l = i & 7;
         const Int3 so = unflat3(s, ns1);
@@ -257,197 +248,177 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_near_tc(
     fence_async_smem();
     if (tid == 0) {
         for (int q = 0; q < NT_STAGES; ++q) {
-            bar_init(su32(&bar_full[q]), W_PN);                // one arrival per producer warp
-            bar_init(su32(&bar_sfull[q]), 1);
+            bar_init(su32(&bar_full[q]), NT_P + 1);               // every producer thread's cp.async + the S bulk copy
             bar_init(su32(&bar_empty[q]), 1);
         }
         bar_init(su32(&bar_d1_full), 1);
+        bar_init(su32(&bar_d1_free), 4);
         for (int h = 0; h < 2; ++h) {
-            bar_init(su32(&bar_a_full[h]), W_AN);
+            bar_init(su32(&bar_b_full[h]), 4);
+            bar_init(su32(&bar_b_free[h]), 1);
+            bar_init(su32(&bar_a_full[h]), NT_AW);
             bar_init(su32(&bar_a_free[h]), 1);
         }
         bar_init(su32(&bar_d2), 1);
         abort_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == W_C0) {
+    if (warp == W_ISS) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_sh)), "r"(NT_TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = tmem_sh, tD1 = tmem + (uint32_t)(2 * N2);
+    const uint32_t tmem = tmem_sh, tD1 = tmem + (uint32_t)(nmh * N2);
 
-    if (warp >= W_C0 && warp < W_P0) {
-        // ---------------------------------------- MMA issuer and D1 -> B converters
-        const int quarter = warp & 3;
-        const int L = quarter * 32 + lane, yz = L >> 6, j = L & 63;
-        unsigned char* dst = B2 + yz * (N2 * 128);
-        const uint32_t id1 = idesc_tf32(N1), id2 = idesc_tf32(N2);
-        const uint32_t a0 = su32(A2), b0 = su32(B2);
-        const int n2mma = 8 * nmh;                               // stage-2 MMAs per slot: (half, Y|Z, k-step)
-        bool ok = true;
-        int kg = 0;
-        for (int i = 0; i <= nsl; ++i) {
-            if (warp == W_C0) {
-                if (lane == 0 && ok) {
-                    // phase i: stage 1 of slot i (i < nsl) with stage 2 of slot i - 1 (i > 0) spread between its K-blocks
-                    const int nkb = (i < nsl) ? s_sl[i].z : 0;
-                    int s2 = 0;                                  // next stage-2 MMA
-                    // stage-2 MMAs up to `upto` (waiting for a half's Ahat when it is not ready)
-                    auto issue_s2 = [&](int upto, bool force) {
-                        (void)force;
-                        while (ok && s2 < upto) {
-                            const int mh = s2 >> 3, yzb = (s2 >> 2) & 1, kk = s2 & 3;
-                            if ((s2 & 7) == 0) {
-                                const uint32_t ab = su32(&bar_a_full[mh]), par = (uint32_t)((i - 1) & 1);
-                                ok = bar_wait(ab, par, status, abort_flag);
-                                if (!ok) return;
-                                tc_fence_after();
-                            }
-                            mma(tmem + (uint32_t)(mh * N2), desc_sw128(a0 + yzb * A_KB + mh * (A_KB / 2) + kk * 32),
-                                desc_sw128(b0 + yzb * N2 * 128 + kk * 32), id2, (i > 1 || yzb > 0 || kk > 0) ? 1u : 0u);
-                            ++s2;
-                            if ((s2 & 7) == 0) commit(su32(&bar_a_free[mh]));
-                        }
-                    };
+    if (warp == W_ISS) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const uint32_t id1 = idesc_f16(N1, true), id2 = idesc_f16(N2, false);
+            const uint32_t a0 = su32(A2), b0 = su32(B2), r0 = su32(ring);
+            bool ok = true;
+            int kg = 0;
+            for (int i = 0; i <= nsl && ok; ++i) {
+                if (i < nsl) {
+                    // stage 1 of slot i into D1 (the converters have read D1 of slot i - 1)
+                    if (i > 0) ok = bar_wait(su32(&bar_d1_free), (uint32_t)((i - 1) & 1), status, abort_flag);
+                    tc_fence_after();
+                    const int nkb = s_sl[i].z;
                     for (int kb = 0; kb < nkb && ok; ++kb, ++kg) {
                         const int q = kg % NT_STAGES;
-                        const uint32_t par = (uint32_t)((kg / NT_STAGES) & 1);
-                        ok = bar_wait(su32(&bar_full[q]), par, status, abort_flag) &&
-                             bar_wait(su32(&bar_sfull[q]), par, status, abort_flag);
+                        ok = bar_wait(su32(&bar_full[q]), (uint32_t)((kg / NT_STAGES) & 1), status, abort_flag);
                         if (!ok) break;
-                        fence_async_smem();                      // the producers' cp.async writes, for the async proxy
                         tc_fence_after();
-                        const uint32_t sa = su32(ring + q * lay.stage_bytes), sb = sa + S_BYTES;
+                        const uint32_t sa = r0 + (uint32_t)(q * lay.stage_bytes), sb = sa + S_BYTES;
 #pragma unroll
-                        for (int kk = 0; kk < NT_KB / 8; ++kk)
-                            mma(tD1, desc_sw128(sa + kk * 32), desc_sw128(sb + kk * 32), id1, (kb > 0 || kk > 0) ? 1u : 0u);
+                        for (int kk = 0; kk < NT_KB / 16; ++kk)
+                            mma(tD1, make_desc(sa + kk * 32, 16, 512, 4), make_desc(sb + kk * 1024, XB_BYTES, 512, 4), id1,
+                                (kb > 0 || kk > 0) ? 1u : 0u);
                         commit(su32(&bar_empty[q]));
-                        if (i > 0) issue_s2(n2mma * (kb + 1) / (nkb + 1), false);
                     }
-                    if (i > 0) issue_s2(n2mma, true);
-                    if (ok && i < nsl) commit(su32(&bar_d1_full));   // S1(i) and S2(i - 1) done: D1 full, B and Ahat free
+                    if (ok) commit(su32(&bar_d1_full));
                 }
-                __syncwarp();
-                ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-            }
-            if (i == nsl) break;
-            // convert D1(i) into B; the four warps meet at a named barrier every slot
-            bool got = ok && bar_wait(su32(&bar_d1_full), (uint32_t)(i & 1), status, abort_flag);
-            got = __all_sync(0xffffffffu, got);
-            if (got) {
-                tc_fence_after();
-                for (int ch = 0; ch < nch; ++ch) {
-                    float v[32];
-                    tmem_ld32(tD1 + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ch * 32), v);
+                if (i > 0 && ok) {
+                    // stage 2 of slot j = i - 1
+                    const int j = i - 1, bsel = j & 1;
+                    const uint32_t par = (uint32_t)((j >> 1) & 1);
+                    ok = bar_wait(su32(&bar_b_full[bsel]), par, status, abort_flag) &&
+                         bar_wait(su32(&bar_a_full[bsel]), par, status, abort_flag);
+                    if (!ok) break;
+                    tc_fence_after();
+                    const uint32_t ab = a0 + (uint32_t)(bsel * A_BYTES), bb = b0 + (uint32_t)(bsel * N2 * 128);
+                    for (int mh = 0; mh < nmh; ++mh)
 #pragma unroll
-                    for (int c = 0; c < 8; ++c)
-                        *reinterpret_cast<uint4*>(dst + sw128(ch * 64 + j, 4 * c, N2)) =
-                            pack_tf32(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+                        for (int kk = 0; kk < 4; ++kk)
+                            mma(tmem + (uint32_t)(mh * N2), make_desc(ab + mh * 128 * 128 + kk * 32, 16, 1024, 2),
+                                make_desc(bb + kk * 32, 16, 1024, 2), id2, (j > 0 || kk > 0) ? 1u : 0u);
+                    commit(su32(&bar_b_free[bsel]));
+                    commit(su32(&bar_a_free[bsel]));
                 }
-                fence_async_smem();
             }
-            ok = ok && got;
-            tc_fence_before();
-            converters_sync();                                   // D1 read, B(i) written
-            tc_fence_after();
-        }
-        if (warp == W_C0 && lane == 0) {
             commit(su32(&bar_d2));
             bar_drain(su32(&bar_d2), 0, status);                 // every MMA finished (also on the abort path)
         }
         __syncwarp();
-    } else if (warp >= W_P0 && warp < W_A1) {
+    } else if (warp >= W_CV0 && warp < W_CV0 + 4) {
+        // ------------------------------------------------- D1 -> B converters
+        // Thread L = TMEM lane (y1|z, target j) of D1: its row of every chain
+        // becomes row (chain, j) of B, columns Y or Z (16-byte chunks 0-3 or 4-7).
+        const int quarter = warp & 3, L = quarter * 32 + lane, yz = L >> 6, j = L & 63;
+        bool ok = true;
+        for (int i = 0; i < nsl; ++i) {
+            ok = ok && bar_wait(su32(&bar_d1_full), (uint32_t)(i & 1), status, abort_flag);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
+            tc_fence_after();
+            float v[3][32];
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch)
+                if (ch < nch) tmem_ld32(tD1 + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ch * 32), v[ch]);
+            tmem_wait_ld();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) bar_arrive(su32(&bar_d1_free));     // D1 may be overwritten by stage 1 of slot i + 1
+            const int bsel = i & 1;
+            if (i >= 2) ok = bar_wait(su32(&bar_b_free[bsel]), (uint32_t)(((i >> 1) - 1) & 1), status, abort_flag);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
+            unsigned char* dst = B2 + bsel * N2 * 128;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                if (ch >= nch) break;
+                const int row = ch * 64 + j;
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    const float* w = v[ch] + 8 * m;
+                    *reinterpret_cast<uint4*>(dst + sw128(row, yz * 4 + m)) =
+                        make_uint4(pack_h2(w[0] * sb, w[1] * sb), pack_h2(w[2] * sb, w[3] * sb),
+                                   pack_h2(w[4] * sb, w[5] * sb), pack_h2(w[6] * sb, w[7] * sb));
+                }
+            }
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) bar_arrive(su32(&bar_b_full[bsel]));
+        }
+    } else if (warp >= W_P0 && warp < W_P0 + W_PN) {
         // -------------------------------------------------- stage-1 producers
-        // Lane (row rr, float octet): each warp instruction copies 8 floats of
-        // 4 source rows; the octet is rotated by the row so that the 4 rows read
-        // different 32-byte chunks (distinct L1 banks), and the shared-memory
-        // destinations of the 32 lanes fall in 32 distinct banks.  Each warp
-        // keeps up to NT_STAGES K-blocks in flight: after issuing K-block kg it
-        // waits for its own copies of K-block kg - (NT_STAGES - 1) and signals
-        // that stage with one arrival per warp.
-        const int p = warp - W_P0;
-        const int rr = p * 4 + (lane & 3), n0 = lane >> 2, twot = 2 * t;
-        const size_t chs = (size_t)nk * 8 * t * 2;             // floats per chain of X
+        // Thread pt: source row r = pt / 4 of the K-block, 16-byte chunk c = pt % 4
+        // of that row's piece (transitions 4c .. 4c + 3) for every chain; the
+        // destination is the MN-major tile of 64-byte rows with the 64-byte swizzle.
+        const int pt = tid - 32 * W_P0, r = pt >> 2, c = pt & 3;
+        const int tq = tpad >> 2;                                   // chunks per piece
+        const size_t chs = (size_t)nk * 8 * tpad;                   // half2 per chain of X
+        const uint32_t doff = (uint32_t)((r >> 3) * 512 + (r & 7) * 64 + (((c ^ (r >> 1)) & 3) << 4));
         bool ok = true;
         int issued = 0;
         for (int kg = 0; kg < nkg; ++kg) {
             const int q = kg % NT_STAGES;
-            if (kg >= NT_STAGES) ok = bar_wait(su32(&bar_empty[q]), (uint32_t)(((kg / NT_STAGES) - 1) & 1), status, abort_flag);
-            if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
+            if (kg >= NT_STAGES) {
+                if (lane == 0) ok = bar_wait(su32(&bar_empty[q]), (uint32_t)(((kg / NT_STAGES) - 1) & 1), status, abort_flag);
+                ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            }
+            if (!ok) break;
             const int i = s_ki[kg] & 0xFFFF, kb = s_ki[kg] >> 16;
             const int4 si = s_sl[i];
-            const int r = kb * NT_KB + rr;
-            const int code = r < si.w ? (int)s_rows[s_rs[i] + r] : -1;
-            unsigned char* Sq = ring + q * lay.stage_bytes;
-            unsigned char* Bq = Sq + S_BYTES;
-            if (p == 0 && lane == 0) {
-                const uint32_t sb = su32(&bar_sfull[q]);
-                bar_arrive_tx(sb, S_BYTES);
-                bulk_copy(su32(Sq), Simg + (size_t)(si.y + kb) * S_BYTES, S_BYTES, sb);
+            const int rr = kb * NT_KB + r;
+            const int code = rr < si.w ? rows[s_rs[i] + rr] : -1;
+            const uint32_t Sq = su32(ring + q * lay.stage_bytes), Xq = Sq + S_BYTES;
+            if (pt == 0) {
+                bar_arrive_tx(su32(&bar_full[q]), S_BYTES);
+                bulk_copy(Sq, Simg + (size_t)(si.y + kb) * S_BYTES, S_BYTES, su32(&bar_full[q]));
             }
-            if (code >= 0) {
-                const int js = code & 0xFF, l = code >> 8;
-                const float* src = X + (((size_t)scell[si.x * 8 + l] * Ndiv + js) * 8 + l) * t * 2;
-                for (int ch = 0; ch < nch; ++ch)
+            const bool live = code >= 0 && c < tq;
+            const __half2* src = X;
+            if (live) {
+                const int js = code & 0xFFFF, l = code >> 16;
+                src = X + (((size_t)scell[si.x * 8 + l] * Ndiv + js) * 8 + l) * tpad + 4 * c;
+            }
 #pragma unroll
-                    for (int fo = 0; fo < 4; ++fo) {
-                        const int nn = (((fo + lane) & 3) << 3) + n0;
-                        if (nn < twot) cp_async4(Bq + sw128(ch * 32 + nn, rr, N1), src + ch * chs + nn);
-                    }
-            }
-            cp_async_commit();
+            for (int ch = 0; ch < 3; ++ch)
+                if (ch < nch) cp_async16(Xq + (uint32_t)(ch * XB_BYTES) + doff, live ? src + ch * chs : X, live ? 16u : 0u);
+            cp_async_arrive_noinc(su32(&bar_full[q]));               // arrives when this thread's copies landed
             ++issued;
-            if (kg >= NT_STAGES - 1) {
-                cp_async_wait_lag();                             // this thread's copies of K-block kg - (NT_STAGES - 1) landed
-                fence_async_smem();
-                __syncwarp();
-                if (lane == 0) bar_arrive(su32(&bar_full[(kg - (NT_STAGES - 1)) % NT_STAGES]));
-            }
         }
         cp_async_wait0();
-        fence_async_smem();
-        __syncwarp();
-        if (ok && lane == 0)                                     // the last NT_STAGES - 1 K-blocks
-            for (int j = std::max(0, issued - (NT_STAGES - 1)); j < issued; ++j) bar_arrive(su32(&bar_full[j % NT_STAGES]));
-        if (p == 0 && lane == 0)                                 // bulk copies in flight must land before exit
-            for (int j = std::max(0, issued - NT_STAGES); j < issued; ++j)
-                bar_drain(su32(&bar_sfull[j % NT_STAGES]), (uint32_t)((j / NT_STAGES) & 1), status);
+        if (pt == 0)                                                 // bulk copies in flight must land before exit
+            for (int jj = std::max(0, issued - NT_STAGES); jj < issued; ++jj)
+                bar_drain(su32(&bar_full[jj % NT_STAGES]), (uint32_t)((jj / NT_STAGES) & 1), status);
     } else {
-        // ------------------------------------------------------ Ahat writers
-        // Items (l, e, pair of e') are fixed per thread: decode them once.  The
-        // slot's head factors are staged one slot ahead by cp.async into
-        // hbuf[slot parity]; the writers never leave the loop early (named
-        // barriers), they skip the work once a wait gave up.
-        const int ta = (warp < W_C0 ? warp : warp - W_A1 + W_C0) * 32 + lane;
-        const int nvv = nv * nv, ncc = nc * nc, nitem = 8 * t * th, per = nvv + ncc + 1;
-        int d0[NT_AMAX], d1[NT_AMAX], d2[NT_AMAX];
-#pragma unroll
-        for (int k = 0; k < NT_AMAX; ++k) {
-            const int it = ta + k * NT_A;
-            d0[k] = d1[k] = d2[k] = -1;
-            if (it < nitem) {
-                const int l = it / (t * th), e = (it / th) % t, qp = it % th;
-                const int n1 = e / nc, n2 = e % nc, ep0 = 2 * qp, ep1 = 2 * qp + 1, has1 = ep1 < t;
-                const int e1 = has1 ? ep1 : ep0;
-                const int hv0 = l * nvv + n1 * nv + ep0 / nc, hv1 = l * nvv + n1 * nv + e1 / nc;
-                const int hm0 = l * ncc + n2 * nc + ep0 % nc, hm1 = l * ncc + n2 * nc + e1 % nc;
-                const int row = (l * t + e) * 2;
-                d0[k] = hv0 | (hv1 << 9) | (hm0 << 18);
-                d1[k] = hm1 | (((int)sw128(row, 4 * qp, NT_M) >> 4) << 9) | (l << 21) | (has1 << 24) | (((l * t + e) >= 64) << 25);
-                d2[k] = (int)sw128(row + 1, 4 * qp, NT_M) >> 4;
-            }
-        }
+        // ------------------------------------------------------- head writers
+        // Item (corner l, transition e, chunk of four e') gives the two D2 rows
+        // (l, e, re|im) of that chunk in the Y and the Z column blocks.
+        const int ta = (warp < W_CV0 ? warp - 1 : warp - 12 + 3) * 32 + lane;
+        const int nvv = nv * nv, ncc = nc * nc, t4 = (t + 3) >> 2, nitem = 8 * t * t4, per = nvv + ncc + 1;
+        const float ia = 1.0f / alpha;
         auto prefetch = [&](int i) {
             const Int3 so = unflat3(s_sl[i].x, ns1);
             const int oa = so.a + smin - rmin, ob = so.b + smin - rmin, oc = so.c + smin - rmin;
             float2* hvS = reinterpret_cast<float2*>(hbuf + (i & 1) * hbb);
             float2* hmS = hvS + 8 * nvv;
             float* hcS = reinterpret_cast<float*>(hmS + 8 * ncc);
-            for (int j = ta; j < 8 * per; j += NT_A) {
-                const int l = j / per, w = j - l * per;
+            for (int jj = ta; jj < 8 * per; jj += NT_A) {
+                const int l = jj / per, w = jj - l * per;
                 const int l1 = (l >> 2) & 1, l2 = (l >> 1) & 1, l3 = l & 1;
                 const int kt = flat3(ci.a + l1, ci.b + l2, ci.c + l3, n);
                 const int r = ((oa - l1) * nr1 + (ob - l2)) * nr1 + (oc - l3);
@@ -460,65 +431,85 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_near_tc(
         prefetch(0);
         cp_async_commit();
         for (int i = 0; i < nsl; ++i) {
-            writers_sync();                                      // every writer is done with slot i - 1's buffer
+            writers_sync();                                      // every writer is done with slot i - 1's factors
             if (i + 1 < nsl) prefetch(i + 1);
             cp_async_commit();
             cp_async_wait1();                                    // this thread's copies for slot i landed
             writers_sync();                                      // everyone's copies for slot i landed
+            const int bsel = i & 1;
+            if (ok && i >= 2) {
+                if (lane == 0) ok = bar_wait(su32(&bar_a_free[bsel]), (uint32_t)(((i >> 1) - 1) & 1), status, abort_flag);
+                ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            }
+            if (!ok) continue;                                   // keep meeting the named barriers
             const float2* hvS = reinterpret_cast<const float2*>(hbuf + (i & 1) * hbb);
             const float2* hmS = hvS + 8 * nvv;
             const float* hcS = reinterpret_cast<const float*>(hmS + 8 * ncc);
-            for (int mh = 0; mh < nmh; ++mh) {
-                if (ok && i > 0) ok = bar_wait(su32(&bar_a_free[mh]), (uint32_t)((i - 1) & 1), status, abort_flag);
-                ok = __all_sync(0xffffffffu, ok);
-                if (!ok) continue;
+            unsigned char* Ab = A2 + bsel * A_BYTES;
+            for (int it = ta; it < nitem; it += NT_A) {
+                const int l = it / (t * t4), e = (it / t4) % t, cq = it % t4;
+                const int n1 = e / nc, n2 = e % nc;
+                float cr[4], cim[4];
 #pragma unroll
-                for (int k = 0; k < NT_AMAX; ++k) {
-                    if (d0[k] < 0 || ((d1[k] >> 25) & 1) != mh) continue;
-                    const int l = (d1[k] >> 21) & 7;
-                    const float2 c0 = cmul(hvS[d0[k] & 511], hmS[(d0[k] >> 18) & 511]);
-                    const float2 c1 = ((d1[k] >> 24) & 1) ? cmul(hvS[(d0[k] >> 9) & 511], hmS[d1[k] & 511])
-                                                          : make_float2(0.f, 0.f);
-                    const float mhc = -hcS[l];
-                    const uint32_t o0 = (uint32_t)(((d1[k] >> 9) & 4095) << 4), o1 = (uint32_t)(d2[k] << 4);
-                    *reinterpret_cast<uint4*>(A2 + o0) = pack_tf32(c0.x, -c0.y, c1.x, -c1.y);
-                    *reinterpret_cast<uint4*>(A2 + o1) = pack_tf32(c0.y, c0.x, c1.y, c1.x);
-                    *reinterpret_cast<uint4*>(A2 + A_KB + o0) = pack_tf32(mhc * c0.x, -mhc * c0.y, mhc * c1.x, -mhc * c1.y);
-                    *reinterpret_cast<uint4*>(A2 + A_KB + o1) = pack_tf32(mhc * c0.y, mhc * c0.x, mhc * c1.y, mhc * c1.x);
+                for (int u = 0; u < 4; ++u) {
+                    const int ep = 4 * cq + u;
+                    cr[u] = 0.f;
+                    cim[u] = 0.f;
+                    if (ep < t) {
+                        const float2 cc = cmul(hvS[l * nvv + n1 * nv + ep / nc], hmS[l * ncc + n2 * nc + ep % nc]);
+                        cr[u] = cc.x * ia;
+                        cim[u] = cc.y * ia;
+                    }
                 }
-                fence_async_smem();
-                __syncwarp();
-                if (lane == 0) bar_arrive(su32(&bar_a_full[mh]));
+                const float mhc = -hcS[l];
+                const int row = (l * t + e) * 2;
+                *reinterpret_cast<uint4*>(Ab + sw128(row, cq)) =
+                    make_uint4(pack_h2(cr[0], -cim[0]), pack_h2(cr[1], -cim[1]), pack_h2(cr[2], -cim[2]), pack_h2(cr[3], -cim[3]));
+                *reinterpret_cast<uint4*>(Ab + sw128(row + 1, cq)) =
+                    make_uint4(pack_h2(cim[0], cr[0]), pack_h2(cim[1], cr[1]), pack_h2(cim[2], cr[2]), pack_h2(cim[3], cr[3]));
+                *reinterpret_cast<uint4*>(Ab + sw128(row, 4 + cq)) =
+                    make_uint4(pack_h2(mhc * cr[0], -mhc * cim[0]), pack_h2(mhc * cr[1], -mhc * cim[1]),
+                               pack_h2(mhc * cr[2], -mhc * cim[2]), pack_h2(mhc * cr[3], -mhc * cim[3]));
+                *reinterpret_cast<uint4*>(Ab + sw128(row + 1, 4 + cq)) =
+                    make_uint4(pack_h2(mhc * cim[0], mhc * cr[0]), pack_h2(mhc * cim[1], mhc * cr[1]),
+                               pack_h2(mhc * cim[2], mhc * cr[2]), pack_h2(mhc * cim[3], mhc * cr[3]));
             }
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) bar_arrive(su32(&bar_a_full[bsel]));
         }
         cp_async_wait0();
     }
 
     // ------------------------------------------------------------- epilogue
-    const bool done = bar_wait(su32(&bar_d2), 0, status, abort_flag);
-    if (__all_sync(0xffffffffu, done) && !*abort_flag) {
+    bool done = true;
+    if (lane == 0) done = bar_wait(su32(&bar_d2), 0, status, abort_flag);
+    done = __shfl_sync(0xffffffffu, done ? 1 : 0, 0) != 0;
+    if (done && !*abort_flag) {
         tc_fence_after();
-        // warp w reads TMEM lanes 32 (w % 4).. of items (half, 32-column chunk) w / 4, w / 4 + 6, ...
+        // warp w reads TMEM lanes 32 (w % 4).. of items (half, 32-column chunk) w / 4, w / 4 + 4, ...
         const int quarter = warp & 3, cg = warp >> 2, nchunk = N2 / 32;
         for (int item = cg; item < nmh * nchunk; item += NT_THREADS / 128) {
             const int mh = item / nchunk, c = item % nchunk, ch = c >> 1, j0 = (c & 1) * 32;
             float v[32];
             tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(mh * N2 + c * 32), v);
+            tmem_wait_ld();
+            const float f = alpha / (xscale[ch] * sb);
             const int row = mh * 128 + quarter * 32 + lane;
             const int pair = row >> 1, ri = row & 1;
             const int l = pair / t, e = pair % t;
 #pragma unroll
             for (int jj = 0; jj < 32; ++jj) {
                 const float other = __shfl_xor_sync(0xffffffffu, v[jj], 1);
-                const int j = j0 + jj;
-                if (ri == 0 && l < 8 && j < Ndiv && interp_active(j, l, nd, nb1))
-                    U[(((size_t)ch * nk + (size_t)cell * Ndiv + j) * 8 + l) * t + e] = make_float2(v[jj], other);
+                const int jt = j0 + jj;
+                if (ri == 0 && l < 8 && jt < Ndiv && interp_active(jt, l, nd, nb1))
+                    U[(((size_t)ch * nk + (size_t)cell * Ndiv + jt) * 8 + l) * t + e] = make_float2(v[jj] * f, other * f);
             }
         }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == W_C0) {
+    if (warp == W_ISS) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NT_TMEM_COLS));
     }
@@ -532,24 +523,31 @@ __global__ void k_near_pattern(const int4* __restrict__ ent, int nent, const flo
     if (i >= nent) return;
     const int4 e = ent[i];
     unsigned char* b = img + (size_t)e.x * S_BYTES;
-    *reinterpret_cast<uint32_t*>(b + sw128(e.y, e.z, 128)) = f2tf32(hd[e.w]);
-    *reinterpret_cast<uint32_t*>(b + sw128(64 + e.y, e.z, 128)) = f2tf32(1.0f);
+    *reinterpret_cast<__half*>(b + sw64(e.y, e.z)) = __float2half_rn(hd[e.w]);
+    *reinterpret_cast<__half*>(b + sw64(64 + e.y, e.z)) = __float2half_rn(1.0f);
 }
 
-size_t near_tc_smem(int nv, int nc, int nch, int nsl, int nkg, int nslot, int nrows) {
+size_t near_tc_smem(int nv, int nc, int nch, int nsl, int nkg, int nslot) {
     const NtLayout lay(nch);
     return 1024 + (size_t)lay.tab_off + 2 * (size_t)hb_bytes(nv, nc) + 20 * (size_t)nsl + 4 * (size_t)nkg +
-           32 * (size_t)nslot + 2 * (size_t)nrows;
+           32 * (size_t)nslot;
+}
+
+// Largest power of two at or below x (x > 0): x = m 2^e with m in [0.5, 1).
+float pow2_floor(double x) {
+    int e = 0;
+    std::frexp(x, &e);
+    return (float)std::ldexp(1.0, e - 1);
 }
 
 }  // namespace
 
 // Decide whether the tensor-core near field serves this handle (FP32 M3 with
-// t <= 16 and N_div <= 64), and build its per-slot source rows and pattern
+// 2 <= t <= 16 and N_div <= 64), and build its per-slot source rows and pattern
 // images from the per-(target, slot) near lists (needs the near head values).
 int bse_near_tc_prepare(bse_ctx* ctx, bse_interp* s, const std::vector<std::vector<NearEntry>>& per_slot) {
     s->nf_tc = 0;
-    if (s->vec_prec != BSE_PREC_F32 || s->t > 16 || s->Ndiv > NT_N || s->scheme != BSE_SCHEME_M3) return BSE_OK;
+    if (s->vec_prec != BSE_PREC_F32 || s->t > 16 || s->t < 2 || s->Ndiv > 64 || s->scheme != BSE_SCHEME_M3) return BSE_OK;
     const int Ndiv = s->Ndiv, nslot = s->nslot;
     std::vector<int4> slots, pent;
     std::vector<int> rows, rowstart, kinfo, loc((size_t)Ndiv * 8, -1);
@@ -577,7 +575,7 @@ int bse_near_tc_prepare(bse_ctx* ctx, bse_interp* s, const std::vector<std::vect
     if (slots.empty() || slots.size() >= 65536) return BSE_OK;
     int maxsm = 0;
     cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
-    const size_t smem = near_tc_smem(s->nv, s->nc, 3, (int)slots.size(), (int)kinfo.size(), nslot, (int)rows.size());
+    const size_t smem = near_tc_smem(s->nv, s->nc, 3, (int)slots.size(), (int)kinfo.size(), nslot);
     if (smem > (size_t)maxsm) return BSE_OK;
     auto upload = [&](void** dst, const void* src, size_t bytes, const char* what) -> int {
         int rc = bse_alloc(ctx, dst, bytes, what);
@@ -603,6 +601,12 @@ int bse_near_tc_prepare(bse_ctx* ctx, bse_interp* s, const std::vector<std::vect
         ctx->err = std::string("near pattern images: ") + cudaGetErrorString(e);
         return BSE_ERR_CUDA;
     }
+    // Operand scales (powers of two): the stage-2 scale s_b from the largest
+    // head value h_max = 1 / kappa^2 and the number of near offsets; the source
+    // scale s_x per chain (bse_near_tc_scales) from the overlap bound.
+    const double hmax = 1.0 / (s->co->kappa * s->co->kappa);
+    s->nf_tc_sb = pow2_floor(1.0 / (hmax * std::sqrt((double)s->n_near)));
+    s->nf_tc_tpad = (s->t + 3) & ~3;
     s->nf_tc_nsl = (int)slots.size();
     s->nf_tc_nkg = (int)kinfo.size();
     s->nf_tc_nrows = (int)rows.size();
@@ -610,22 +614,30 @@ int bse_near_tc_prepare(bse_ctx* ctx, bse_interp* s, const std::vector<std::vect
     return BSE_OK;
 }
 
-int bse_near_tc_launch(bse_ctx* ctx, const bse_interp* s, int nchains, const void* X, void* U) {
+// s_x for a vector of 2-norm `norm`: the largest power of two with
+// s_x dbound norm <= 2^15 (dbound bounds ||d_v||_F ||d_c||_F over the pieces).
+float bse_near_tc_xscale(const bse_interp* s, double norm) {
+    const double b = std::max(s->dbound * std::max(norm, 1e-300), 1e-300);
+    return pow2_floor(32768.0 / b);
+}
+
+int bse_near_tc_launch(bse_ctx* ctx, const bse_interp* s, int nchains, const void* Xh, const float* xscale, void* U) {
     // at most three chains per launch (TMEM: 160 columns per chain)
     for (int c0 = 0; c0 < nchains; c0 += 3) {
         const int nch = std::min(3, nchains - c0);
-        const size_t smem = near_tc_smem(s->nv, s->nc, nch, s->nf_tc_nsl, s->nf_tc_nkg, s->nslot, s->nf_tc_nrows);
+        const size_t smem = near_tc_smem(s->nv, s->nc, nch, s->nf_tc_nsl, s->nf_tc_nkg, s->nslot);
         // handles of different sizes share the kernel's attribute: only ever raise it
         cudaFuncAttributes fa;
         BSE_CUDA_TRY(ctx, cudaFuncGetAttributes(&fa, k_near_tc));
         if ((size_t)fa.maxDynamicSharedSizeBytes < smem)
             BSE_CUDA_TRY(ctx, cudaFuncSetAttribute(k_near_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        const size_t off = (size_t)c0 * s->nk * 8 * s->t;
+        const size_t xoff = (size_t)c0 * s->nk * 8 * s->nf_tc_tpad;
+        const size_t uoff = (size_t)c0 * s->nk * 8 * s->t;
         k_near_tc<<<s->co->nkc, NT_THREADS, smem, ctx->stream>>>(
-            (const float*)((const float2*)X + off), s->d_tc_rows, s->d_tc_slots, s->d_tc_rowstart, s->d_tc_kinfo,
-            s->nf_tc_nsl, s->nf_tc_nkg, s->nf_tc_nrows, s->d_tc_simg, (const float2*)s->d_Hv, (const float2*)s->d_Hc,
+            (const __half2*)Xh + xoff, s->nf_tc_tpad, s->d_tc_rows, s->d_tc_slots, s->d_tc_rowstart, s->d_tc_kinfo,
+            s->nf_tc_nsl, s->nf_tc_nkg, s->d_tc_simg, (const float2*)s->d_Hv, (const float2*)s->d_Hc,
             (const float*)s->d_hc, s->n, s->nd, s->nv, s->nc, s->nb1, s->smin, s->ns1, s->rmin, s->nr1, nch,
-            (float2*)U + off, ctx->d_status);
+            xscale + c0, s->nf_tc_sb, (float)s->co->alpha, (float2*)U + uoff, ctx->d_status);
     }
     return BSE_OK;
 }

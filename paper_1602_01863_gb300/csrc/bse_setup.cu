@@ -452,9 +452,27 @@ namespace {
 
 // Replace the model's dense tables by the caller's (bse_dense_inputs), after
 // k_dense_tables has written the model's.
+// Largest Frobenius norm of the caller's overlap blocks over the pieces of
+// non-zero weight (host arrays [nk][8][nb][nb] complex128).
+double max_block_norm(const double* d, const bse_interp* s, int nb) {
+    double best = 0.0;
+    for (int kd = 0; kd < s->nk; ++kd)
+        for (int l = 0; l < 8; ++l) {
+            if (!interp_active(kd % s->Ndiv, l, s->nd, s->nb1)) continue;
+            const double* p = d + ((size_t)kd * 8 + l) * nb * nb * 2;
+            double f = 0.0;
+            for (int q = 0; q < 2 * nb * nb; ++q) f += p[q] * p[q];
+            best = std::max(best, std::sqrt(f));
+        }
+    return best;
+}
+
 template <typename T>
 int apply_dense_inputs(bse_ctx* ctx, bse_interp* s, const bse_dense_inputs* in) {
     using V = typename Cx<T>::V;
+    const double bv = in->Dv ? max_block_norm(in->Dv, s, s->nv) : std::sqrt((double)s->nv);
+    const double bc = in->Dc ? max_block_norm(in->Dc, s, s->nc) : std::sqrt((double)s->nc);
+    s->dbound = bv * bc;
     cudaStream_t st = ctx->stream;
     const long long N = s->N, nDv = (long long)s->nk * 8 * s->nv * s->nv, nDc = (long long)s->nk * 8 * s->nc * s->nc;
     const long long most = std::max(std::max(N, nDv), nDc);
@@ -513,6 +531,7 @@ int setup_interp_typed(bse_ctx* ctx, bse_interp* s, const bse_dense_inputs* dens
         ctx->err = std::string("dense set-up kernels: ") + cudaGetErrorString(e);
         return BSE_ERR_CUDA;
     }
+    s->dbound = std::sqrt((double)nv) * std::sqrt((double)nc);
     if (dense) TRY(apply_dense_inputs<T>(ctx, s, dense));
     // scratch
     const size_t nvec = BSE_MAX_CHAINS;
@@ -642,6 +661,16 @@ int setup_interp_typed(bse_ctx* ctx, bse_interp* s, const bse_dense_inputs* dens
             return BSE_ERR_CUDA;
         }
         TRY(bse_near_tc_prepare(ctx, s, per_slot));
+        if (s->nf_tc) {
+            // FP16 piece scales for unit-norm vectors (every Lanczos vector), and
+            // room for the scales bse_apply_h computes from its inputs' norms
+            const float xs = bse_near_tc_xscale(s, 1.0 + 1e-3);
+            const float h4[4] = {xs, xs, xs, xs};
+            TRY(bse_alloc(ctx, (void**)&s->d_xscale, sizeof(float) * 4, "piece scales"));
+            TRY(bse_alloc(ctx, (void**)&s->d_xscale_gen, sizeof(float) * 4, "piece scales"));
+            BSE_CUDA_TRY(ctx, cudaMemcpy(s->d_xscale, h4, sizeof(h4), cudaMemcpyHostToDevice));
+            BSE_CUDA_TRY(ctx, cudaMemcpy(s->d_xscale_gen, h4, sizeof(h4), cudaMemcpyHostToDevice));
+        }
     }
     if (c->kc_prec == BSE_PREC_BF16) TRY(bse_tc_prepare(ctx, s));
     return BSE_OK;
