@@ -181,7 +181,8 @@ struct bse_interp {
     int4* d_tc_slots = nullptr;      // per slot {slot, first K-block, K-blocks, rows}
     int* d_tc_rowstart = nullptr;    // per slot, first row
     int* d_tc_kinfo = nullptr;       // per K-block: slot ordinal | K-block in slot << 16
-    unsigned char* d_tc_simg = nullptr;   // near pattern images, 16 KB per K-block
+    unsigned char* d_tc_simg = nullptr;   // near pattern images, 8 KB per K-block
+    unsigned char* d_tc_aimg = nullptr;   // head images, 4 KB per (coarse point, relative offset)
     int nf_force_cuda_cores = 0;     // BSE_NF_CUDA_CORES: keep the CUDA-core near-field kernels
     void* d_hd = nullptr;            // T [n_near]   h_head at dense near offsets
     void* d_Hv = nullptr;            // V [nkc][nrel][nv*nv]

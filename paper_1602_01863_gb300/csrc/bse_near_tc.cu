@@ -21,26 +21,29 @@
 // Stage 2 (per slot): the converters read D1 back from TMEM, scale it by s_b
 // and write the K-major FP16 operand
 //   B_s[(chain, k), (Y|Z, e', re|im)] = s_b s_x y1(k, s), s_b s_x z(k, s);
-// the head writers form, from the per-cell head factors,
-//   Ahat_s[(l,e,.), (Y,e',.)] = [[Re c, -Im c], [Im c, Re c]],  c = A(k~_l, k~_s)[e][e'] / alpha,
-//   Ahat_s[(l,e,.), (Z,e',.)] = the same for -h_head(q_c(l, s)) c,
-// and the issuer accumulates
+// the head operand of the slot is eight pre-swizzled FP16 images, one per
+// target corner l, built at set-up for every (coarse point k~, relative offset r):
+//   Ahat[(e,.), (Y,e',.)] = [[Re c, -Im c], [Im c, Re c]],  c = A(k~, k~ + r)[e][e'] / alpha,
+//   Ahat[(e,.), (Z,e',.)] = the same for -h_head(q_c(r)) c,
+// (32 rows: e padded to 16; 4 KB each) and loaded by bulk copies; the issuer
+// accumulates
 //   D2 [256 = (l, e, re|im)] x [64 * chains] += Ahat_s [256 x 64] * B_s^T.
 // The epilogue writes u = alpha D2 / (s_x s_b).  The scales keep every FP16
 // operand inside its normal range: |x s_x| <= 2^15 from the bound
 // |x| <= ||d_v||_F ||d_c||_F ||psi||_2, and |y1 s_x s_b|, |z s_x s_b| <= 2^15 from
 // |y1| <= h_max sqrt(n_near) ||x||_2; c / 1 and h_head c are at most h_max.
 //
-// Warp roles (512 threads, one CTA per coarse cell):
+// Warp roles (384 threads, one CTA per coarse cell):
 //   warp 0         MMA issuer (lane 0) and TMEM owner
+//   warp 1         head loader (lane 0): eight 4 KB bulk copies per slot
 //   warps 4-7      converters (TMEM lane quarter = warp % 4)
 //   warps 8-11     producers: per K-block one thread issues the S-image bulk
 //                  copy, every thread 16-byte cp.async gathers of X rows, and
 //                  cp.async.mbarrier.arrive signals the stage when they land
-//   warps 1-3, 12-15  head writers (Ahat), head factors staged one slot ahead
+//   (warps 2-3 only join the epilogue)
 // Pipeline: a 6-stage ring for stage 1; D1 single (TMEM), B and Ahat double
-// buffered (shared memory), so the converters and head writers of slot i work
-// while the tensor cores run stage 2 of slot i - 1 and stage 1 of slot i + 1.
+// buffered (shared memory), so the converters and the head loader of slot i
+// work while the tensor cores run stage 2 of slot i - 1 and stage 1 of slot i + 1.
 // Constraints: 2 <= t <= 16, N_div <= 64, FP32 vectors, <= 3 chains per launch.
 // Every wait is bounded; on expiry the kernel raises bit 1 of the status word,
 // every role leaves its loop, the copies and MMAs in flight are drained and
@@ -56,19 +59,19 @@
 
 namespace {
 
-constexpr int NT_THREADS = 512;
+constexpr int NT_THREADS = 384;
 constexpr int NT_KB = 32;                    // source rows per stage-1 K-block
 constexpr int NT_STAGES = 6;                 // stage-1 ring depth
 constexpr int S_BYTES = 128 * NT_KB * 2;     // one S image K-block: 8 KB (FP16, K-major, 64 B rows)
 constexpr int XB_BYTES = NT_KB * 64;         // X tile per chain: 32 rows x 64 B (MN-major, 64-byte swizzle)
 constexpr int A_BYTES = 256 * 128;           // Ahat: 256 rows x 64 FP16 (128 B) = 32 KB
+constexpr int AH_BYTES = 32 * 128;           // one head image: 32 rows (e < 16, re|im) x 128 B
 constexpr int NT_TMEM_COLS = 512;
 constexpr int W_ISS = 0;                     // MMA issuer
 constexpr int W_CV0 = 4;                     // converters: warps 4-7
 constexpr int W_P0 = 8, W_PN = 4;            // producers: warps 8-11
 constexpr int NT_P = 32 * W_PN;              // producer threads
-constexpr int NT_AW = 7;                     // head writers: warps 1-3, 12-15
-constexpr int NT_A = 32 * NT_AW;
+constexpr int W_AL = 1;                      // head loader
 constexpr long long NT_WAIT_CYCLES = 400000000LL;   // ~0.2 s; a whole launch takes well under 10 ms
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -176,17 +179,9 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-__device__ __forceinline__ void writers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(NT_A) : "memory"); }
-
 __device__ __forceinline__ uint32_t pack_h2(float a, float b) {
     const __half2 h = __floats2half2_rn(a, b);
     return *reinterpret_cast<const uint32_t*>(&h);
-}
-
-// Shared-memory bytes of one head-factor buffer: Hv, Hc of the 8 target corners
-// for one slot, then h_head(q_c) of the 8 corners.
-__host__ __device__ __forceinline__ int hb_bytes(int nv, int nc) {
-    return ((8 * (nv * nv + nc * nc) * 8 + 32) + 15) & ~15;
 }
 
 // Shared-memory layout (bytes from the 1024-aligned base) for `nch` chains.
@@ -198,16 +193,16 @@ struct NtLayout {
         b_off = 2 * A_BYTES;                              // Ahat: [2 buffers][256 rows][128 B]
         ring_off = b_off + 2 * N2 * 128;                  // B: [2 buffers][N2 rows][128 B]
         stage_bytes = S_BYTES + nch * XB_BYTES;           // ring stage: S K-block | X tile per chain
-        tab_off = ring_off + NT_STAGES * stage_bytes;     // head-factor buffers [2], then slot tables
+        tab_off = ring_off + NT_STAGES * stage_bytes;     // slot tables
     }
 };
 
 __global__ void __launch_bounds__(NT_THREADS, 1) k_near_tc(
     const __half2* __restrict__ X, int tpad, const int* __restrict__ rows, const int4* __restrict__ slots,
     const int* __restrict__ rowstart, const int* __restrict__ kinfo, int nsl, int nkg,
-    const unsigned char* __restrict__ Simg, const float2* __restrict__ Hv, const float2* __restrict__ Hc,
-    const float* __restrict__ hc, int n, int nd, int nv, int nc, int nb1, int smin, int ns1, int rmin, int nr1,
-    int nch, const float* __restrict__ xscale, float sb, float alpha, float2* __restrict__ U, int* __restrict__ status) {
+    const unsigned char* __restrict__ Simg, const unsigned char* __restrict__ Aimg, int n, int nd, int nv, int nc,
+    int nb1, int smin, int ns1, int rmin, int nr1, int nch, const float* __restrict__ xscale, float sb, float alpha,
+    float2* __restrict__ U, int* __restrict__ status) {
     // an earlier launch on this context gave up a wait: skip (the host reports BSE_ERR_TIMEOUT)
     if (*reinterpret_cast<volatile int*>(status) & 2) return;
     extern __shared__ unsigned char raw[];
@@ -219,18 +214,15 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_near_tc(
     volatile int* abort_flag = &abort_sh;
     const int t = nv * nc, Ndiv = nd * nd * nd, nslot = ns1 * ns1 * ns1, nrel = nr1 * nr1 * nr1;
     const int nk = n * n * n * Ndiv;
-    // D2 rows (l, e, re|im) = 2 (l t + e) + re|im; the second 128-row half holds
-    // anything only when 16 t > 128
-    const int nmh = (16 * t > 128) ? 2 : 1;
+    // D2 rows (l, e, re|im) = 32 l + 2 e + re|im, e < 16: two 128-row halves
+    constexpr int nmh = 2;
     const NtLayout lay(nch);
     const int N1 = lay.N1, N2 = lay.N2;
     const int cell = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     unsigned char* A2 = sm;
     unsigned char* B2 = sm + lay.b_off;
     unsigned char* ring = sm + lay.ring_off;
-    const int hbb = hb_bytes(nv, nc);
-    unsigned char* hbuf = sm + lay.tab_off;                     // [2][hbb]  head factors, slot parity
-    int4* s_sl = reinterpret_cast<int4*>(hbuf + 2 * hbb);       // [nsl]
+    int4* s_sl = reinterpret_cast<int4*>(sm + lay.tab_off);     // [nsl]
     int* s_rs = reinterpret_cast<int*>(s_sl + nsl);             // [nsl]
     int* s_ki = s_rs + nsl;                                     // [nkg]
     int* scell = s_ki + nkg;                                    // [nslot][8] source cells
@@ -256,7 +248,7 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_near_tc(
         for (int h = 0; h < 2; ++h) {
             bar_init(su32(&bar_b_full[h]), 4);
             bar_init(su32(&bar_b_free[h]), 1);
-            bar_init(su32(&bar_a_full[h]), NT_AW);
+            bar_init(su32(&bar_a_full[h]), 1);                     // the loader's expect_tx (8 bulk copies)
             bar_init(su32(&bar_a_free[h]), 1);
         }
         bar_init(su32(&bar_d2), 1);
@@ -404,81 +396,33 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_near_tc(
         if (pt == 0)                                                 // bulk copies in flight must land before exit
             for (int jj = std::max(0, issued - NT_STAGES); jj < issued; ++jj)
                 bar_drain(su32(&bar_full[jj % NT_STAGES]), (uint32_t)((jj / NT_STAGES) & 1), status);
-    } else {
-        // ------------------------------------------------------- head writers
-        // Item (corner l, transition e, chunk of four e') gives the two D2 rows
-        // (l, e, re|im) of that chunk in the Y and the Z column blocks.
-        const int ta = (warp < W_CV0 ? warp - 1 : warp - 12 + 3) * 32 + lane;
-        const int nvv = nv * nv, ncc = nc * nc, t4 = (t + 3) >> 2, nitem = 8 * t * t4, per = nvv + ncc + 1;
-        const float ia = 1.0f / alpha;
-        auto prefetch = [&](int i) {
-            const Int3 so = unflat3(s_sl[i].x, ns1);
-            const int oa = so.a + smin - rmin, ob = so.b + smin - rmin, oc = so.c + smin - rmin;
-            float2* hvS = reinterpret_cast<float2*>(hbuf + (i & 1) * hbb);
-            float2* hmS = hvS + 8 * nvv;
-            float* hcS = reinterpret_cast<float*>(hmS + 8 * ncc);
-            for (int jj = ta; jj < 8 * per; jj += NT_A) {
-                const int l = jj / per, w = jj - l * per;
-                const int l1 = (l >> 2) & 1, l2 = (l >> 1) & 1, l3 = l & 1;
-                const int kt = flat3(ci.a + l1, ci.b + l2, ci.c + l3, n);
-                const int r = ((oa - l1) * nr1 + (ob - l2)) * nr1 + (oc - l3);
-                if (w < nvv) cp_async8(hvS + l * nvv + w, Hv + ((size_t)kt * nrel + r) * nvv + w);
-                else if (w < nvv + ncc) cp_async8(hmS + l * ncc + (w - nvv), Hc + ((size_t)kt * nrel + r) * ncc + (w - nvv));
-                else cp_async4(hcS + l, hc + r);
-            }
-        };
-        bool ok = true;
-        prefetch(0);
-        cp_async_commit();
-        for (int i = 0; i < nsl; ++i) {
-            writers_sync();                                      // every writer is done with slot i - 1's factors
-            if (i + 1 < nsl) prefetch(i + 1);
-            cp_async_commit();
-            cp_async_wait1();                                    // this thread's copies for slot i landed
-            writers_sync();                                      // everyone's copies for slot i landed
-            const int bsel = i & 1;
-            if (ok && i >= 2) {
-                if (lane == 0) ok = bar_wait(su32(&bar_a_free[bsel]), (uint32_t)(((i >> 1) - 1) & 1), status, abort_flag);
-                ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-            }
-            if (!ok) continue;                                   // keep meeting the named barriers
-            const float2* hvS = reinterpret_cast<const float2*>(hbuf + (i & 1) * hbb);
-            const float2* hmS = hvS + 8 * nvv;
-            const float* hcS = reinterpret_cast<const float*>(hmS + 8 * ncc);
-            unsigned char* Ab = A2 + bsel * A_BYTES;
-            for (int it = ta; it < nitem; it += NT_A) {
-                const int l = it / (t * t4), e = (it / t4) % t, cq = it % t4;
-                const int n1 = e / nc, n2 = e % nc;
-                float cr[4], cim[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int ep = 4 * cq + u;
-                    cr[u] = 0.f;
-                    cim[u] = 0.f;
-                    if (ep < t) {
-                        const float2 cc = cmul(hvS[l * nvv + n1 * nv + ep / nc], hmS[l * ncc + n2 * nc + ep % nc]);
-                        cr[u] = cc.x * ia;
-                        cim[u] = cc.y * ia;
-                    }
+    } else if (warp == W_AL) {
+        // -------------------------------------------------------- head loader
+        // Slot i: the images of (k~_l, k~_s - k~_l) for the eight target corners l.
+        if (lane == 0) {
+            bool ok = true;
+            int issued = 0;
+            for (int i = 0; i < nsl && ok; ++i) {
+                const int bsel = i & 1;
+                if (i >= 2) ok = bar_wait(su32(&bar_a_free[bsel]), (uint32_t)(((i >> 1) - 1) & 1), status, abort_flag);
+                if (!ok) break;
+                const Int3 so = unflat3(s_sl[i].x, ns1);
+                const int oa = so.a + smin - rmin, ob = so.b + smin - rmin, oc = so.c + smin - rmin;
+                const uint32_t ab = su32(A2 + bsel * A_BYTES), bar = su32(&bar_a_full[bsel]);
+                bar_arrive_tx(bar, 8 * AH_BYTES);
+                for (int l = 0; l < 8; ++l) {
+                    const int l1 = (l >> 2) & 1, l2 = (l >> 1) & 1, l3 = l & 1;
+                    const int kt = flat3(ci.a + l1, ci.b + l2, ci.c + l3, n);
+                    const int r = ((oa - l1) * nr1 + (ob - l2)) * nr1 + (oc - l3);
+                    bulk_copy(ab + (uint32_t)(l * AH_BYTES), Aimg + ((size_t)kt * nrel + r) * AH_BYTES, AH_BYTES, bar);
                 }
-                const float mhc = -hcS[l];
-                const int row = (l * t + e) * 2;
-                *reinterpret_cast<uint4*>(Ab + sw128(row, cq)) =
-                    make_uint4(pack_h2(cr[0], -cim[0]), pack_h2(cr[1], -cim[1]), pack_h2(cr[2], -cim[2]), pack_h2(cr[3], -cim[3]));
-                *reinterpret_cast<uint4*>(Ab + sw128(row + 1, cq)) =
-                    make_uint4(pack_h2(cim[0], cr[0]), pack_h2(cim[1], cr[1]), pack_h2(cim[2], cr[2]), pack_h2(cim[3], cr[3]));
-                *reinterpret_cast<uint4*>(Ab + sw128(row, 4 + cq)) =
-                    make_uint4(pack_h2(mhc * cr[0], -mhc * cim[0]), pack_h2(mhc * cr[1], -mhc * cim[1]),
-                               pack_h2(mhc * cr[2], -mhc * cim[2]), pack_h2(mhc * cr[3], -mhc * cim[3]));
-                *reinterpret_cast<uint4*>(Ab + sw128(row + 1, 4 + cq)) =
-                    make_uint4(pack_h2(mhc * cim[0], mhc * cr[0]), pack_h2(mhc * cim[1], mhc * cr[1]),
-                               pack_h2(mhc * cim[2], mhc * cr[2]), pack_h2(mhc * cim[3], mhc * cr[3]));
+                ++issued;
             }
-            fence_async_smem();
-            __syncwarp();
-            if (lane == 0) bar_arrive(su32(&bar_a_full[bsel]));
+            // copies in flight must land before exit
+            for (int jj = std::max(0, issued - 2); jj < issued; ++jj)
+                bar_drain(su32(&bar_a_full[jj & 1]), (uint32_t)((jj >> 1) & 1), status);
         }
-        cp_async_wait0();
+        __syncwarp();
     }
 
     // ------------------------------------------------------------- epilogue
@@ -496,13 +440,12 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_near_tc(
             tmem_wait_ld();
             const float f = alpha / (xscale[ch] * sb);
             const int row = mh * 128 + quarter * 32 + lane;
-            const int pair = row >> 1, ri = row & 1;
-            const int l = pair / t, e = pair % t;
+            const int ri = row & 1, l = row >> 5, e = (row & 31) >> 1;
 #pragma unroll
             for (int jj = 0; jj < 32; ++jj) {
                 const float other = __shfl_xor_sync(0xffffffffu, v[jj], 1);
                 const int jt = j0 + jj;
-                if (ri == 0 && l < 8 && jt < Ndiv && interp_active(jt, l, nd, nb1))
+                if (ri == 0 && e < t && jt < Ndiv && interp_active(jt, l, nd, nb1))
                     U[(((size_t)ch * nk + (size_t)cell * Ndiv + jt) * 8 + l) * t + e] = make_float2(v[jj] * f, other * f);
             }
         }
@@ -527,10 +470,34 @@ __global__ void k_near_pattern(const int4* __restrict__ ent, int nent, const flo
     *reinterpret_cast<__half*>(b + sw64(64 + e.y, e.z)) = __float2half_rn(1.0f);
 }
 
+// Head images (stage-2 operand blocks), one per (coarse point k~, relative
+// offset r): 32 rows (e < 16, re|im) x 64 FP16 columns (Y | Z, e' < 16, re|im),
+// K-major with the 128-byte swizzle; c = A(k~, k~ + r)[e][e'] / alpha from the
+// head factors Hv = alpha O^v, Hc = O^c, zero outside e, e' < t.
+__global__ void __launch_bounds__(256) k_head_images(const float2* __restrict__ Hv, const float2* __restrict__ Hc,
+                                                     const float* __restrict__ hc, int nrel, int nv, int nc,
+                                                     float alpha, unsigned char* __restrict__ img) {
+    const int blk = blockIdx.x, r = blk % nrel, row = threadIdx.x >> 3, chunk = threadIdx.x & 7;
+    const int t = nv * nc, e = row >> 1, ri = row & 1, yz = chunk >> 2, cq = chunk & 3;
+    const float2* hv = Hv + (size_t)blk * nv * nv;
+    const float2* hm = Hc + (size_t)blk * nc * nc;
+    const float f = (yz ? -hc[r] : 1.0f) / alpha;
+    uint32_t w[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int ep = 4 * cq + u;
+        float2 c = make_float2(0.f, 0.f);
+        if (e < t && ep < t) c = cmul(hv[(e / nc) * nv + ep / nc], hm[(e % nc) * nc + ep % nc]);
+        c = make_float2(c.x * f, c.y * f);
+        w[u] = ri == 0 ? pack_h2(c.x, -c.y) : pack_h2(c.y, c.x);
+    }
+    *reinterpret_cast<uint4*>(img + (size_t)blk * AH_BYTES + sw128(row, chunk)) = make_uint4(w[0], w[1], w[2], w[3]);
+}
+
 size_t near_tc_smem(int nv, int nc, int nch, int nsl, int nkg, int nslot) {
     const NtLayout lay(nch);
-    return 1024 + (size_t)lay.tab_off + 2 * (size_t)hb_bytes(nv, nc) + 20 * (size_t)nsl + 4 * (size_t)nkg +
-           32 * (size_t)nslot;
+    (void)nv; (void)nc;
+    return 1024 + (size_t)lay.tab_off + 20 * (size_t)nsl + 4 * (size_t)nkg + 32 * (size_t)nslot;
 }
 
 // Largest power of two at or below x (x > 0): x = m 2^e with m in [0.5, 1).
@@ -601,6 +568,16 @@ int bse_near_tc_prepare(bse_ctx* ctx, bse_interp* s, const std::vector<std::vect
         ctx->err = std::string("near pattern images: ") + cudaGetErrorString(e);
         return BSE_ERR_CUDA;
     }
+    const long long nimg = (long long)s->co->nkc * s->nrel;
+    if ((rc = bse_alloc(ctx, (void**)&s->d_tc_aimg, (size_t)nimg * AH_BYTES, "near head images")) != BSE_OK) return rc;
+    k_head_images<<<(int)nimg, 256, 0, ctx->stream>>>((const float2*)s->d_Hv, (const float2*)s->d_Hc, (const float*)s->d_hc,
+                                                      s->nrel, s->nv, s->nc, (float)s->co->alpha, s->d_tc_aimg);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        ctx->err = std::string("near head images: ") + cudaGetErrorString(e);
+        return BSE_ERR_CUDA;
+    }
     // Operand scales (powers of two): the stage-2 scale s_b from the largest
     // head value h_max = 1 / kappa^2 and the number of near offsets; the source
     // scale s_x per chain (bse_near_tc_scales) from the overlap bound.
@@ -635,8 +612,8 @@ int bse_near_tc_launch(bse_ctx* ctx, const bse_interp* s, int nchains, const voi
         const size_t uoff = (size_t)c0 * s->nk * 8 * s->t;
         k_near_tc<<<s->co->nkc, NT_THREADS, smem, ctx->stream>>>(
             (const __half2*)Xh + xoff, s->nf_tc_tpad, s->d_tc_rows, s->d_tc_slots, s->d_tc_rowstart, s->d_tc_kinfo,
-            s->nf_tc_nsl, s->nf_tc_nkg, s->d_tc_simg, (const float2*)s->d_Hv, (const float2*)s->d_Hc,
-            (const float*)s->d_hc, s->n, s->nd, s->nv, s->nc, s->nb1, s->smin, s->ns1, s->rmin, s->nr1, nch,
+            s->nf_tc_nsl, s->nf_tc_nkg, s->d_tc_simg, s->d_tc_aimg, s->n, s->nd, s->nv, s->nc, s->nb1, s->smin,
+            s->ns1, s->rmin, s->nr1, nch,
             xscale + c0, s->nf_tc_sb, (float)s->co->alpha, (float2*)U + uoff, ctx->d_status);
     }
     return BSE_OK;
