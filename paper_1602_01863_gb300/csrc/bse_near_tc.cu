@@ -199,7 +199,7 @@ struct NtLayout {
 
 __global__ void __launch_bounds__(NT_THREADS, 1) k_near_tc(
     const __half2* __restrict__ X, int tpad, const int* __restrict__ rows, const int4* __restrict__ slots,
-    const int* __restrict__ rowstart, const int* __restrict__ kinfo, int nsl, int nkg,
+    const int* __restrict__ rowstart, const int* __restrict__ kinfo, int nsl, int nkg, int nrows,
     const unsigned char* __restrict__ Simg, const unsigned char* __restrict__ Aimg, int n, int nd, int nv, int nc,
     int nb1, int smin, int ns1, int rmin, int nr1, int nch, const float* __restrict__ xscale, float sb, float alpha,
     float2* __restrict__ U, int* __restrict__ status) {
@@ -226,9 +226,14 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_near_tc(
     int* s_rs = reinterpret_cast<int*>(s_sl + nsl);             // [nsl]
     int* s_ki = s_rs + nsl;                                     // [nkg]
     int* scell = s_ki + nkg;                                    // [nslot][8] source cells
+    unsigned short* s_rows = reinterpret_cast<unsigned short*>(scell + nslot * 8);   // [nrows] js | corner << 8
     const Int3 ci = unflat3(cell, n);
     for (int i = tid; i < nsl; i += NT_THREADS) { s_sl[i] = slots[i]; s_rs[i] = rowstart[i]; }
     for (int i = tid; i < nkg; i += NT_THREADS) s_ki[i] = kinfo[i];
+    for (int i = tid; i < nrows; i += NT_THREADS) {
+        const int code = rows[i];
+        s_rows[i] = (unsigned short)((code & 0xFF) | ((code >> 16) << 8));
+    }
     for (int i = tid; i < nslot * 8; i += NT_THREADS) {
         const int s = i >> 3, l = i & 7;
         const Int3 so = unflat3(s, ns1);
@@ -281,6 +286,7 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_near_tc(
                         const int q = kg % NT_STAGES;
                         ok = bar_wait(su32(&bar_full[q]), (uint32_t)((kg / NT_STAGES) & 1), status, abort_flag);
                         if (!ok) break;
+                        fence_async_smem();                      // the producers' cp.async writes, for the async proxy
                         tc_fence_after();
                         const uint32_t sa = r0 + (uint32_t)(q * lay.stage_bytes), sb = sa + S_BYTES;
 #pragma unroll
@@ -374,7 +380,7 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_near_tc(
             const int i = s_ki[kg] & 0xFFFF, kb = s_ki[kg] >> 16;
             const int4 si = s_sl[i];
             const int rr = kb * NT_KB + r;
-            const int code = rr < si.w ? rows[s_rs[i] + rr] : -1;
+            const int code = rr < si.w ? (int)s_rows[s_rs[i] + rr] : -1;
             const uint32_t Sq = su32(ring + q * lay.stage_bytes), Xq = Sq + S_BYTES;
             if (pt == 0) {
                 bar_arrive_tx(su32(&bar_full[q]), S_BYTES);
@@ -383,7 +389,7 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_near_tc(
             const bool live = code >= 0 && c < tq;
             const __half2* src = X;
             if (live) {
-                const int js = code & 0xFFFF, l = code >> 16;
+                const int js = code & 0xFF, l = code >> 8;
                 src = X + (((size_t)scell[si.x * 8 + l] * Ndiv + js) * 8 + l) * tpad + 4 * c;
             }
 #pragma unroll
@@ -494,10 +500,9 @@ __global__ void __launch_bounds__(256) k_head_images(const float2* __restrict__ 
     *reinterpret_cast<uint4*>(img + (size_t)blk * AH_BYTES + sw128(row, chunk)) = make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-size_t near_tc_smem(int nv, int nc, int nch, int nsl, int nkg, int nslot) {
+size_t near_tc_smem(int nch, int nsl, int nkg, int nslot, int nrows) {
     const NtLayout lay(nch);
-    (void)nv; (void)nc;
-    return 1024 + (size_t)lay.tab_off + 20 * (size_t)nsl + 4 * (size_t)nkg + 32 * (size_t)nslot;
+    return 1024 + (size_t)lay.tab_off + 20 * (size_t)nsl + 4 * (size_t)nkg + 32 * (size_t)nslot + 2 * (size_t)nrows;
 }
 
 // Largest power of two at or below x (x > 0): x = m 2^e with m in [0.5, 1).
@@ -542,7 +547,7 @@ int bse_near_tc_prepare(bse_ctx* ctx, bse_interp* s, const std::vector<std::vect
     if (slots.empty() || slots.size() >= 65536) return BSE_OK;
     int maxsm = 0;
     cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
-    const size_t smem = near_tc_smem(s->nv, s->nc, 3, (int)slots.size(), (int)kinfo.size(), nslot);
+    const size_t smem = near_tc_smem(3, (int)slots.size(), (int)kinfo.size(), nslot, (int)rows.size());
     if (smem > (size_t)maxsm) return BSE_OK;
     auto upload = [&](void** dst, const void* src, size_t bytes, const char* what) -> int {
         int rc = bse_alloc(ctx, dst, bytes, what);
@@ -602,7 +607,7 @@ int bse_near_tc_launch(bse_ctx* ctx, const bse_interp* s, int nchains, const voi
     // at most three chains per launch (TMEM: 160 columns per chain)
     for (int c0 = 0; c0 < nchains; c0 += 3) {
         const int nch = std::min(3, nchains - c0);
-        const size_t smem = near_tc_smem(s->nv, s->nc, nch, s->nf_tc_nsl, s->nf_tc_nkg, s->nslot);
+        const size_t smem = near_tc_smem(nch, s->nf_tc_nsl, s->nf_tc_nkg, s->nslot, s->nf_tc_nrows);
         // handles of different sizes share the kernel's attribute: only ever raise it
         cudaFuncAttributes fa;
         BSE_CUDA_TRY(ctx, cudaFuncGetAttributes(&fa, k_near_tc));
@@ -612,7 +617,7 @@ int bse_near_tc_launch(bse_ctx* ctx, const bse_interp* s, int nchains, const voi
         const size_t uoff = (size_t)c0 * s->nk * 8 * s->t;
         k_near_tc<<<s->co->nkc, NT_THREADS, smem, ctx->stream>>>(
             (const __half2*)Xh + xoff, s->nf_tc_tpad, s->d_tc_rows, s->d_tc_slots, s->d_tc_rowstart, s->d_tc_kinfo,
-            s->nf_tc_nsl, s->nf_tc_nkg, s->d_tc_simg, s->d_tc_aimg, s->n, s->nd, s->nv, s->nc, s->nb1, s->smin,
+            s->nf_tc_nsl, s->nf_tc_nkg, s->nf_tc_nrows, s->d_tc_simg, s->d_tc_aimg, s->n, s->nd, s->nv, s->nc, s->nb1, s->smin,
             s->ns1, s->rmin, s->nr1, nch,
             xscale + c0, s->nf_tc_sb, (float)s->co->alpha, (float2*)U + uoff, ctx->d_status);
     }
