@@ -177,10 +177,10 @@ struct bse_interp {
     int nf_tc_nsl = 0;               // slots that reach the cell
     int nf_tc_nkg = 0;               // their stage-1 K-blocks
     int nf_tc_nrows = 0;             // their source rows (all slots)
-    int* d_tc_rows = nullptr;        // source rows of every slot: js | corner << 16
+    void* d_tc_rows = nullptr;       // [K-blocks][32] source rows: js | corner << 8, 0xFFFF none (ushort)
     int4* d_tc_slots = nullptr;      // per slot {slot, first K-block, K-blocks, rows}
-    int* d_tc_rowstart = nullptr;    // per slot, first row
-    int* d_tc_kinfo = nullptr;       // per K-block: slot ordinal | K-block in slot << 16
+    int* d_tc_rowstart = nullptr;    // (unused)
+    void* d_tc_kinfo = nullptr;      // [K-blocks] slot of each K-block (uchar)
     unsigned char* d_tc_simg = nullptr;   // near pattern images, 8 KB per K-block
     unsigned char* d_tc_aimg = nullptr;   // head images, 4 KB per (coarse point, relative offset)
     int nf_force_cuda_cores = 0;     // BSE_NF_CUDA_CORES: keep the CUDA-core near-field kernels

@@ -41,9 +41,10 @@
 //                  copy, every thread 16-byte cp.async gathers of X rows, and
 //                  cp.async.mbarrier.arrive signals the stage when they land
 //   (warps 2-3 only join the epilogue)
-// Pipeline: a 6-stage ring for stage 1; D1 single (TMEM), B and Ahat double
-// buffered (shared memory), so the converters and the head loader of slot i
-// work while the tensor cores run stage 2 of slot i - 1 and stage 1 of slot i + 1.
+// Pipeline: a 4-stage ring for stage 1; D1 single (TMEM), B double and Ahat
+// triple buffered (shared memory), so the converters and the head loader of
+// slot i work while the tensor cores run stage 2 of slot i - 1 and stage 1 of
+// slot i + 1.
 // Constraints: 2 <= t <= 16, N_div <= 64, FP32 vectors, <= 3 chains per launch.
 // Every wait is bounded; on expiry the kernel raises bit 1 of the status word,
 // every role leaves its loop, the copies and MMAs in flight are drained and
@@ -61,7 +62,8 @@ namespace {
 
 constexpr int NT_THREADS = 384;
 constexpr int NT_KB = 32;                    // source rows per stage-1 K-block
-constexpr int NT_STAGES = 6;                 // stage-1 ring depth
+constexpr int NT_STAGES = 4;                 // stage-1 ring depth
+constexpr int NT_NA = 3;                     // head-operand buffers
 constexpr int S_BYTES = 128 * NT_KB * 2;     // one S image K-block: 8 KB (FP16, K-major, 64 B rows)
 constexpr int XB_BYTES = NT_KB * 64;         // X tile per chain: 32 rows x 64 B (MN-major, 64-byte swizzle)
 constexpr int A_BYTES = 256 * 128;           // Ahat: 256 rows x 64 FP16 (128 B) = 32 KB
@@ -190,7 +192,7 @@ struct NtLayout {
     __host__ __device__ NtLayout(int nch) {
         N1 = 32 * nch;
         N2 = 64 * nch;
-        b_off = 2 * A_BYTES;                              // Ahat: [2 buffers][256 rows][128 B]
+        b_off = NT_NA * A_BYTES;                          // Ahat: [3 buffers][256 rows][128 B]
         ring_off = b_off + 2 * N2 * 128;                  // B: [2 buffers][N2 rows][128 B]
         stage_bytes = S_BYTES + nch * XB_BYTES;           // ring stage: S K-block | X tile per chain
         tab_off = ring_off + NT_STAGES * stage_bytes;     // slot tables
@@ -198,8 +200,8 @@ struct NtLayout {
 };
 
 __global__ void __launch_bounds__(NT_THREADS, 1) k_near_tc(
-    const __half2* __restrict__ X, int tpad, const int* __restrict__ rows, const int4* __restrict__ slots,
-    const int* __restrict__ rowstart, const int* __restrict__ kinfo, int nsl, int nkg, int nrows,
+    const __half2* __restrict__ X, int tpad, const int4* __restrict__ slots,
+    const unsigned short* __restrict__ krows, const unsigned char* __restrict__ kslot, int nsl, int nkg,
     const unsigned char* __restrict__ Simg, const unsigned char* __restrict__ Aimg, int n, int nd, int nv, int nc,
     int nb1, int smin, int ns1, int rmin, int nr1, int nch, const float* __restrict__ xscale, float sb, float alpha,
     float2* __restrict__ U, int* __restrict__ status) {
@@ -208,7 +210,7 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_near_tc(
     extern __shared__ unsigned char raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~(uintptr_t)1023);
     __shared__ uint64_t bar_full[NT_STAGES], bar_empty[NT_STAGES];
-    __shared__ uint64_t bar_d1_full, bar_d1_free, bar_b_full[2], bar_b_free[2], bar_a_full[2], bar_a_free[2], bar_d2;
+    __shared__ uint64_t bar_d1_full, bar_d1_free, bar_b_full[2], bar_b_free[2], bar_a_full[NT_NA], bar_a_free[NT_NA], bar_d2;
     __shared__ uint32_t tmem_sh;
     __shared__ int abort_sh;
     volatile int* abort_flag = &abort_sh;
@@ -223,17 +225,14 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_near_tc(
     unsigned char* B2 = sm + lay.b_off;
     unsigned char* ring = sm + lay.ring_off;
     int4* s_sl = reinterpret_cast<int4*>(sm + lay.tab_off);     // [nsl]
-    int* s_rs = reinterpret_cast<int*>(s_sl + nsl);             // [nsl]
-    int* s_ki = s_rs + nsl;                                     // [nkg]
-    int* scell = s_ki + nkg;                                    // [nslot][8] source cells
-    unsigned short* s_rows = reinterpret_cast<unsigned short*>(scell + nslot * 8);   // [nrows] js | corner << 8
+    int* scell = reinterpret_cast<int*>(s_sl + nsl);            // [nslot][8] source cells
+    unsigned short* s_krow = reinterpret_cast<unsigned short*>(scell + nslot * 8);   // [nkg][32] js | corner << 8
+    unsigned char* s_kslot = reinterpret_cast<unsigned char*>(s_krow + (size_t)nkg * NT_KB);   // [nkg] slot
     const Int3 ci = unflat3(cell, n);
-    for (int i = tid; i < nsl; i += NT_THREADS) { s_sl[i] = slots[i]; s_rs[i] = rowstart[i]; }
-    for (int i = tid; i < nkg; i += NT_THREADS) s_ki[i] = kinfo[i];
-    for (int i = tid; i < nrows; i += NT_THREADS) {
-        const int code = rows[i];
-        s_rows[i] = (unsigned short)((code & 0xFF) | ((code >> 16) << 8));
-    }
+    for (int i = tid; i < nsl; i += NT_THREADS) s_sl[i] = slots[i];
+    for (int i = tid; i < nkg * NT_KB / 2; i += NT_THREADS)
+        reinterpret_cast<uint32_t*>(s_krow)[i] = reinterpret_cast<const uint32_t*>(krows)[i];
+    for (int i = tid; i < nkg; i += NT_THREADS) s_kslot[i] = kslot[i];
     for (int i = tid; i < nslot * 8; i += NT_THREADS) {
         const int s = i >> 3, l = i & 7;
         const Int3 so = unflat3(s, ns1);
@@ -253,6 +252,8 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_near_tc(
         for (int h = 0; h < 2; ++h) {
             bar_init(su32(&bar_b_full[h]), 4);
             bar_init(su32(&bar_b_free[h]), 1);
+        }
+        for (int h = 0; h < NT_NA; ++h) {
             bar_init(su32(&bar_a_full[h]), 1);                     // the loader's expect_tx (8 bulk copies)
             bar_init(su32(&bar_a_free[h]), 1);
         }
@@ -299,20 +300,19 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_near_tc(
                 }
                 if (i > 0 && ok) {
                     // stage 2 of slot j = i - 1
-                    const int j = i - 1, bsel = j & 1;
-                    const uint32_t par = (uint32_t)((j >> 1) & 1);
-                    ok = bar_wait(su32(&bar_b_full[bsel]), par, status, abort_flag) &&
-                         bar_wait(su32(&bar_a_full[bsel]), par, status, abort_flag);
+                    const int j = i - 1, bsel = j & 1, asel = j % NT_NA;
+                    ok = bar_wait(su32(&bar_b_full[bsel]), (uint32_t)((j >> 1) & 1), status, abort_flag) &&
+                         bar_wait(su32(&bar_a_full[asel]), (uint32_t)((j / NT_NA) & 1), status, abort_flag);
                     if (!ok) break;
                     tc_fence_after();
-                    const uint32_t ab = a0 + (uint32_t)(bsel * A_BYTES), bb = b0 + (uint32_t)(bsel * N2 * 128);
+                    const uint32_t ab = a0 + (uint32_t)(asel * A_BYTES), bb = b0 + (uint32_t)(bsel * N2 * 128);
                     for (int mh = 0; mh < nmh; ++mh)
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk)
                             mma(tmem + (uint32_t)(mh * N2), make_desc(ab + mh * 128 * 128 + kk * 32, 16, 1024, 2),
                                 make_desc(bb + kk * 32, 16, 1024, 2), id2, (j > 0 || kk > 0) ? 1u : 0u);
                     commit(su32(&bar_b_free[bsel]));
-                    commit(su32(&bar_a_free[bsel]));
+                    commit(su32(&bar_a_free[asel]));
                 }
             }
             commit(su32(&bar_d2));
@@ -377,20 +377,17 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_near_tc(
                 ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             }
             if (!ok) break;
-            const int i = s_ki[kg] & 0xFFFF, kb = s_ki[kg] >> 16;
-            const int4 si = s_sl[i];
-            const int rr = kb * NT_KB + r;
-            const int code = rr < si.w ? (int)s_rows[s_rs[i] + rr] : -1;
+            const int code = s_krow[kg * NT_KB + r], sl = s_kslot[kg];
             const uint32_t Sq = su32(ring + q * lay.stage_bytes), Xq = Sq + S_BYTES;
             if (pt == 0) {
                 bar_arrive_tx(su32(&bar_full[q]), S_BYTES);
-                bulk_copy(Sq, Simg + (size_t)(si.y + kb) * S_BYTES, S_BYTES, su32(&bar_full[q]));
+                bulk_copy(Sq, Simg + (size_t)kg * S_BYTES, S_BYTES, su32(&bar_full[q]));
             }
-            const bool live = code >= 0 && c < tq;
+            const bool live = code != 0xFFFF && c < tq;
             const __half2* src = X;
             if (live) {
                 const int js = code & 0xFF, l = code >> 8;
-                src = X + (((size_t)scell[si.x * 8 + l] * Ndiv + js) * 8 + l) * tpad + 4 * c;
+                src = X + (((size_t)scell[sl * 8 + l] * Ndiv + js) * 8 + l) * tpad + 4 * c;
             }
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch)
@@ -409,8 +406,8 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_near_tc(
             bool ok = true;
             int issued = 0;
             for (int i = 0; i < nsl && ok; ++i) {
-                const int bsel = i & 1;
-                if (i >= 2) ok = bar_wait(su32(&bar_a_free[bsel]), (uint32_t)(((i >> 1) - 1) & 1), status, abort_flag);
+                const int bsel = i % NT_NA;
+                if (i >= NT_NA) ok = bar_wait(su32(&bar_a_free[bsel]), (uint32_t)(((i / NT_NA) - 1) & 1), status, abort_flag);
                 if (!ok) break;
                 const Int3 so = unflat3(s_sl[i].x, ns1);
                 const int oa = so.a + smin - rmin, ob = so.b + smin - rmin, oc = so.c + smin - rmin;
@@ -425,8 +422,8 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_near_tc(
                 ++issued;
             }
             // copies in flight must land before exit
-            for (int jj = std::max(0, issued - 2); jj < issued; ++jj)
-                bar_drain(su32(&bar_a_full[jj & 1]), (uint32_t)((jj >> 1) & 1), status);
+            for (int jj = std::max(0, issued - NT_NA); jj < issued; ++jj)
+                bar_drain(su32(&bar_a_full[jj % NT_NA]), (uint32_t)((jj / NT_NA) & 1), status);
         }
         __syncwarp();
     }
@@ -500,9 +497,9 @@ __global__ void __launch_bounds__(256) k_head_images(const float2* __restrict__ 
     *reinterpret_cast<uint4*>(img + (size_t)blk * AH_BYTES + sw128(row, chunk)) = make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-size_t near_tc_smem(int nch, int nsl, int nkg, int nslot, int nrows) {
+size_t near_tc_smem(int nch, int nsl, int nkg, int nslot) {
     const NtLayout lay(nch);
-    return 1024 + (size_t)lay.tab_off + 20 * (size_t)nsl + 4 * (size_t)nkg + 32 * (size_t)nslot + 2 * (size_t)nrows;
+    return 1024 + (size_t)lay.tab_off + 16 * (size_t)nsl + 32 * (size_t)nslot + (2 * NT_KB + 1) * (size_t)nkg;
 }
 
 // Largest power of two at or below x (x > 0): x = m 2^e with m in [0.5, 1).
@@ -522,7 +519,9 @@ int bse_near_tc_prepare(bse_ctx* ctx, bse_interp* s, const std::vector<std::vect
     if (s->vec_prec != BSE_PREC_F32 || s->t > 16 || s->t < 2 || s->Ndiv > 64 || s->scheme != BSE_SCHEME_M3) return BSE_OK;
     const int Ndiv = s->Ndiv, nslot = s->nslot;
     std::vector<int4> slots, pent;
-    std::vector<int> rows, rowstart, kinfo, loc((size_t)Ndiv * 8, -1);
+    std::vector<int> loc((size_t)Ndiv * 8, -1);
+    std::vector<unsigned short> krows;
+    std::vector<unsigned char> kslot;
     int kstart = 0;
     for (int sl = 0; sl < nslot; ++sl) {
         std::vector<int> used;
@@ -539,15 +538,20 @@ int bse_near_tc_prepare(bse_ctx* ctx, bse_interp* s, const std::vector<std::vect
                 pent.push_back(make_int4(kstart + r / NT_KB, j, r % NT_KB, en.near_idx));
             }
         slots.push_back(make_int4(sl, kstart, nkb, R));
-        rowstart.push_back((int)rows.size());
-        for (int r = 0; r < R; ++r) rows.push_back((used[r] / 8) | ((used[r] % 8) << 16));
-        for (int kb = 0; kb < nkb; ++kb) kinfo.push_back(ord | (kb << 16));
+        for (int kb = 0; kb < nkb; ++kb) {
+            for (int r = 0; r < NT_KB; ++r) {
+                const int rr = kb * NT_KB + r;
+                krows.push_back(rr < R ? (unsigned short)((used[rr] / 8) | ((used[rr] % 8) << 8)) : (unsigned short)0xFFFF);
+            }
+            kslot.push_back((unsigned char)sl);
+        }
+        (void)ord;
         kstart += nkb;
     }
-    if (slots.empty() || slots.size() >= 65536) return BSE_OK;
+    if (slots.empty() || nslot > 256) return BSE_OK;
     int maxsm = 0;
     cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
-    const size_t smem = near_tc_smem(3, (int)slots.size(), (int)kinfo.size(), nslot, (int)rows.size());
+    const size_t smem = near_tc_smem(3, (int)slots.size(), kstart, nslot);
     if (smem > (size_t)maxsm) return BSE_OK;
     auto upload = [&](void** dst, const void* src, size_t bytes, const char* what) -> int {
         int rc = bse_alloc(ctx, dst, bytes, what);
@@ -557,10 +561,9 @@ int bse_near_tc_prepare(bse_ctx* ctx, bse_interp* s, const std::vector<std::vect
     };
     int rc;
     int4* d_pent = nullptr;
-    if ((rc = upload((void**)&s->d_tc_rows, rows.data(), sizeof(int) * rows.size(), "near rows")) != BSE_OK) return rc;
+    if ((rc = upload((void**)&s->d_tc_rows, krows.data(), sizeof(unsigned short) * krows.size(), "near rows")) != BSE_OK) return rc;
     if ((rc = upload((void**)&s->d_tc_slots, slots.data(), sizeof(int4) * slots.size(), "near slots")) != BSE_OK) return rc;
-    if ((rc = upload((void**)&s->d_tc_rowstart, rowstart.data(), sizeof(int) * rowstart.size(), "near row starts")) != BSE_OK) return rc;
-    if ((rc = upload((void**)&s->d_tc_kinfo, kinfo.data(), sizeof(int) * kinfo.size(), "near K-blocks")) != BSE_OK) return rc;
+    if ((rc = upload((void**)&s->d_tc_kinfo, kslot.data(), kslot.size(), "near K-block slots")) != BSE_OK) return rc;
     if ((rc = bse_alloc(ctx, (void**)&s->d_tc_simg, (size_t)kstart * S_BYTES, "near pattern images")) != BSE_OK) return rc;
     if ((rc = upload((void**)&d_pent, pent.data(), sizeof(int4) * pent.size(), "near pattern entries")) != BSE_OK) return rc;
     BSE_CUDA_TRY(ctx, cudaMemsetAsync(s->d_tc_simg, 0, (size_t)kstart * S_BYTES, ctx->stream));
@@ -590,8 +593,8 @@ int bse_near_tc_prepare(bse_ctx* ctx, bse_interp* s, const std::vector<std::vect
     s->nf_tc_sb = pow2_floor(1.0 / (hmax * std::sqrt((double)s->n_near)));
     s->nf_tc_tpad = (s->t + 3) & ~3;
     s->nf_tc_nsl = (int)slots.size();
-    s->nf_tc_nkg = (int)kinfo.size();
-    s->nf_tc_nrows = (int)rows.size();
+    s->nf_tc_nkg = kstart;
+    s->nf_tc_nrows = (int)krows.size();
     s->nf_tc = 1;
     return BSE_OK;
 }
@@ -607,7 +610,7 @@ int bse_near_tc_launch(bse_ctx* ctx, const bse_interp* s, int nchains, const voi
     // at most three chains per launch (TMEM: 160 columns per chain)
     for (int c0 = 0; c0 < nchains; c0 += 3) {
         const int nch = std::min(3, nchains - c0);
-        const size_t smem = near_tc_smem(nch, s->nf_tc_nsl, s->nf_tc_nkg, s->nslot, s->nf_tc_nrows);
+        const size_t smem = near_tc_smem(nch, s->nf_tc_nsl, s->nf_tc_nkg, s->nslot);
         // handles of different sizes share the kernel's attribute: only ever raise it
         cudaFuncAttributes fa;
         BSE_CUDA_TRY(ctx, cudaFuncGetAttributes(&fa, k_near_tc));
@@ -616,8 +619,8 @@ int bse_near_tc_launch(bse_ctx* ctx, const bse_interp* s, int nchains, const voi
         const size_t xoff = (size_t)c0 * s->nk * 8 * s->nf_tc_tpad;
         const size_t uoff = (size_t)c0 * s->nk * 8 * s->t;
         k_near_tc<<<s->co->nkc, NT_THREADS, smem, ctx->stream>>>(
-            (const __half2*)Xh + xoff, s->nf_tc_tpad, s->d_tc_rows, s->d_tc_slots, s->d_tc_rowstart, s->d_tc_kinfo,
-            s->nf_tc_nsl, s->nf_tc_nkg, s->nf_tc_nrows, s->d_tc_simg, s->d_tc_aimg, s->n, s->nd, s->nv, s->nc, s->nb1, s->smin,
+            (const __half2*)Xh + xoff, s->nf_tc_tpad, s->d_tc_slots, (const unsigned short*)s->d_tc_rows,
+            (const unsigned char*)s->d_tc_kinfo, s->nf_tc_nsl, s->nf_tc_nkg, s->d_tc_simg, s->d_tc_aimg, s->n, s->nd, s->nv, s->nc, s->nb1, s->smin,
             s->ns1, s->rmin, s->nr1, nch,
             xscale + c0, s->nf_tc_sb, (float)s->co->alpha, (float2*)U + uoff, ctx->d_status);
     }
