@@ -55,6 +55,9 @@ extern "C" {
 /* ----------------------------------------------------------------- schemes */
 #define BSE_SCHEME_M1   0  /* Method 1: interpolation everywhere (Sec. 4)           */
 #define BSE_SCHEME_M3   1  /* Method 3: M1 plus divergence treatment on near pairs  */
+#define BSE_SCHEME_M2   2  /* Method 2: the coefficients of Eq. diverg interpolated
+                              for every pair and divided by the dense q; the whole
+                              H is stored (complex128, N <= 16384)                 */
 #define BSE_NB1        16  /* OR-flag: one-neighbour weights (Eq. eqRL, f = 1 on
                               the nearest coarse corner) instead of trilinear 8NB   */
 #define BSE_NF_CUDA_CORES 32 /* OR-flag: apply the M3 near field on the CUDA cores
@@ -176,6 +179,12 @@ typedef struct bse_dense_inputs {
  * With BF16 K_c the set-up autotunes the tensor-core apply: it times a few
  * splits of the K_c stream over the SMs on this K_c and keeps the fastest
  * (cached per shape for the process).
+ * BSE_SCHEME_M2 (Sec. 4, Method 2) builds the dense interpolated Hamiltonian
+ *   H = diag(Delta E) + (1/N_div)[(F A F^H) h_head(q_dense) + F (K_c - A h_head(q_coarse)) F^H]
+ * for every pair (no width; F of Eq. interpwfn, A the head for every coarse pair)
+ * once, stored as complex128 [N][N], and every H application is a dense
+ * product with it: complex128 K_c and vectors, N <= 16384 (else
+ * BSE_ERR_UNSUPPORTED), the Yukawa direct term (h_const = 0).
  * `dense` (nullable) replaces the model's dense tables (bse_dense_inputs).
  * Errors: BSE_ERR_ARG (n_div < 1; M3 with width_w >= n / 2, where the near
  * region would wrap around the zone; bad flags; non-finite dense inputs),
@@ -260,6 +269,15 @@ int bse_set_stop_rule(bse_ctx* ctx, double tol, int check_every, double s_eps, d
 int bse_haydock_run(bse_ctx* ctx, bse_interp* const* sys, int nsys, const int* npol,
                     const double* pol_dirs, int nsteps, int flags, double* a, double* b,
                     double* pnorm2, int* steps_done);
+
+/* Testing aid for the failure path: the clock-cycle budget of the bounded
+ * mbarrier waits in the pipeline of the tensor-core K_c apply (`cycles` = 0
+ * restores the default, about 2 s).  A budget too short for a normal launch
+ * makes its first wait give up: the kernel raises its status bit, drains its
+ * copies and MMAs under the default budget, frees its tensor memory and
+ * returns, and the call returns BSE_ERR_TIMEOUT with the status word cleared,
+ * so the context stays usable.  Errors: BSE_ERR_ARG (cycles < 0). */
+int bse_ctx_set_wait_limit(bse_ctx* ctx, long long cycles);
 
 /* Kernel-class device times of the last BSE_PROFILE run, averaged per
  * launch, in ms: [0] restrict, [1] K_c apply, [2] prolong+diagonal,

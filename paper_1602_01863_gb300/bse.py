@@ -26,7 +26,7 @@ BSE_ERR_UNSUPPORTED = -5
 BSE_WARN_BREAKDOWN = 1
 
 PREC_F64, PREC_F32, PREC_BF16 = 0, 1, 2
-SCHEME_M1, SCHEME_M3, NB1, NF_CUDA_CORES = 0, 1, 16, 32
+SCHEME_M1, SCHEME_M3, SCHEME_M2, NB1, NF_CUDA_CORES = 0, 1, 2, 16, 32
 REORTH_CGS2, USE_GRAPH, PROFILE, STOP_CONVERGED = 1, 2, 4, 8
 
 KERNEL_CLASSES = ("restrict", "kc_apply", "prolong", "near_field", "lanczos")
@@ -36,7 +36,7 @@ EXPORTED = ("bse_version", "bse_ctx_create", "bse_ctx_destroy", "bse_last_error"
             "bse_dipoles", "bse_apply_h", "bse_apply_h_noalloc", "bse_haydock_run", "bse_last_kernel_times",
             "bse_spectrum", "bse_mlp_param_count", "bse_mlp_create", "bse_mlp_free", "bse_mlp_get_params",
             "bse_mlp_forward", "bse_mlp_gradients", "bse_mlp_train_step", "bse_pairs_generate",
-            "bse_interp_set_learned", "bse_set_stop_rule")
+            "bse_interp_set_learned", "bse_set_stop_rule", "bse_ctx_set_wait_limit")
 
 
 class BseError(RuntimeError):
@@ -89,6 +89,7 @@ def load(path: str | None = None):
     lib.bse_interp_setup.argtypes = [_P, _P, C.c_int, C.c_int, C.c_double, C.c_int, C.POINTER(bse_dense_inputs),
                                      C.POINTER(_P)]
     lib.bse_set_stop_rule.argtypes = [_P, C.c_double, C.c_int, C.c_double, C.c_double, C.c_int, _D]
+    lib.bse_ctx_set_wait_limit.argtypes = [_P, C.c_longlong]
     lib.bse_free_interp.argtypes = [_P]
     lib.bse_free_interp.restype = None
     lib.bse_interp_info.argtypes = [_P, C.POINTER(C.c_longlong)]
@@ -250,6 +251,10 @@ class Context:
                                               C.byref(din) if din is not None else None, C.byref(h)))
         del keep
         return Interp(self, h, coarse)
+
+    # -- bse_ctx_set_wait_limit (testing aid for the failure path)
+    def bse_ctx_set_wait_limit(self, cycles: int) -> None:
+        self._check(self.lib.bse_ctx_set_wait_limit(self.h, int(cycles)))
 
     # -- bse_set_stop_rule
     def bse_set_stop_rule(self, tol: float, check_every: int, s_eps: float, eta: float, omega: np.ndarray) -> None:

@@ -42,7 +42,7 @@ void free_interp(bse_interp* s) {
                     s->d_vec[1], s->d_vec[2], s->d_part_dot, s->d_part_nrm, s->d_a, s->d_aim, s->d_b, s->d_stop,
                     s->d_basis, s->d_cgs_part, s->d_cgs_h, s->d_pairs, s->d_clist, s->d_cstart,
                     s->d_lker, s->d_lgrid, s->d_tw_fwd, s->d_tc_rows, s->d_tc_slots,
-                    s->d_tc_rowstart, s->d_tc_kinfo, s->d_tc_simg, s->d_tc_aimg, s->d_xscale, s->d_xscale_gen};
+                    s->d_tc_rowstart, s->d_tc_kinfo, s->d_tc_simg, s->d_tc_aimg, s->d_xscale, s->d_xscale_gen, s->d_H2};
     for (void* p : ptrs) cudaFree(p);
     bse_tc_release(s);
     delete s;
@@ -191,7 +191,7 @@ int bse_interp_setup(bse_ctx* ctx, const bse_coarse* c, int n_div, int scheme, d
     if (!c) return set_arg_error(ctx, "coarse handle is NULL");
     if (n_div < 1 || n_div > 16) return set_arg_error(ctx, "n_div must be in 1..16");
     const int base = scheme & ~(BSE_NB1 | BSE_NF_CUDA_CORES);
-    if (base != BSE_SCHEME_M1 && base != BSE_SCHEME_M3) return set_arg_error(ctx, "unknown scheme");
+    if (base != BSE_SCHEME_M1 && base != BSE_SCHEME_M2 && base != BSE_SCHEME_M3) return set_arg_error(ctx, "unknown scheme");
     if (vec_prec != BSE_PREC_F64 && vec_prec != BSE_PREC_F32) return set_arg_error(ctx, "vec_prec must be F64 or F32");
     if ((c->kc_prec == BSE_PREC_F64) != (vec_prec == BSE_PREC_F64)) {
         ctx->err = "supported (K_c, vector) precisions: (F64, F64), (F32, F32), (BF16, F32)";
@@ -201,6 +201,18 @@ int bse_interp_setup(bse_ctx* ctx, const bse_coarse* c, int n_div, int scheme, d
         if (!std::isfinite(width_w) || width_w < 0.0 || 2.0 * width_w >= (double)c->n)
             return set_arg_error(ctx, "M3 width must satisfy 0 <= w < n/2 (near region inside half the zone)");
         if (c->h_const) return set_arg_error(ctx, "M3 needs the Yukawa direct term (h_const = 0)");
+    }
+    if (base == BSE_SCHEME_M2) {
+        if (c->h_const) return set_arg_error(ctx, "M2 needs the Yukawa direct term (h_const = 0)");
+        if (c->kc_prec != BSE_PREC_F64 || vec_prec != BSE_PREC_F64) {
+            ctx->err = "M2 (stored dense H) is built for complex128 K_c and vectors";
+            return BSE_ERR_UNSUPPORTED;
+        }
+        const long long Nd = (long long)c->nkc * n_div * n_div * n_div * c->t;
+        if (Nd > 16384) {
+            ctx->err = "M2 stores the dense H: N must be <= 16384";
+            return BSE_ERR_UNSUPPORTED;
+        }
     }
     const long long nk = (long long)c->nkc * n_div * n_div * n_div;
     if (nk * c->t > (1LL << 31) - 1) { ctx->err = "dense dimension above 2^31"; return BSE_ERR_UNSUPPORTED; }
@@ -301,6 +313,13 @@ int bse_set_stop_rule(bse_ctx* ctx, double tol, int check_every, double s_eps, d
     ctx->stop_seps = s_eps;
     ctx->stop_eta = eta;
     ctx->stop_set = 1;
+    return BSE_OK;
+}
+
+int bse_ctx_set_wait_limit(bse_ctx* ctx, long long cycles) {
+    if (!ctx) return BSE_ERR_ARG;
+    if (cycles < 0) return set_arg_error(ctx, "wait limit must be >= 0 (0: default)");
+    ctx->wait_cycles = cycles;
     return BSE_OK;
 }
 

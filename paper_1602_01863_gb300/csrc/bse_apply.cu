@@ -1309,6 +1309,55 @@ __global__ void k_cont_frac(const double* __restrict__ a, const double* __restri
     eps[idx] = make_double2(1.0 - pref * pn2[ch] * gr, -pref * pn2[ch] * gi);
 }
 
+// Method 2 application w = H psi with the stored dense H (complex128 [N][N]),
+// one warp per row (grid-stride over rows), every chain per row; block
+// partials of <psi, w> for the Lanczos a_i.
+constexpr int kM2Warps = 8;
+__global__ void __launch_bounds__(32 * kM2Warps) k_m2_apply(const double2* __restrict__ H, const double2* __restrict__ psi,
+                                                            int N, int nchains, double2* __restrict__ w,
+                                                            double2* __restrict__ part) {
+    __shared__ double2 red[BSE_MAX_CHAINS][kM2Warps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double2 dot[BSE_MAX_CHAINS];
+#pragma unroll
+    for (int ch = 0; ch < BSE_MAX_CHAINS; ++ch) dot[ch] = make_double2(0.0, 0.0);
+    for (int r = blockIdx.x * kM2Warps + warp; r < N; r += gridDim.x * kM2Warps) {
+        double2 acc[BSE_MAX_CHAINS];
+#pragma unroll
+        for (int ch = 0; ch < BSE_MAX_CHAINS; ++ch) acc[ch] = make_double2(0.0, 0.0);
+        const double2* hr = H + (size_t)r * N;
+        for (int j = lane; j < N; j += 32) {
+            const double2 h = hr[j];
+#pragma unroll
+            for (int ch = 0; ch < BSE_MAX_CHAINS; ++ch)
+                if (ch < nchains) acc[ch] = cadd(acc[ch], cmul(h, psi[(size_t)ch * N + j]));
+        }
+#pragma unroll
+        for (int ch = 0; ch < BSE_MAX_CHAINS; ++ch) {
+            if (ch >= nchains) break;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                acc[ch].x += __shfl_xor_sync(0xffffffffu, acc[ch].x, o);
+                acc[ch].y += __shfl_xor_sync(0xffffffffu, acc[ch].y, o);
+            }
+            if (lane == 0) {
+                w[(size_t)ch * N + r] = acc[ch];
+                dot[ch] = cadd(dot[ch], cmulc(psi[(size_t)ch * N + r], acc[ch]));
+            }
+        }
+    }
+    if (lane == 0)
+        for (int ch = 0; ch < nchains; ++ch) red[ch][warp] = dot[ch];
+    __syncthreads();
+    if (threadIdx.x < nchains) {
+        double2 sum = make_double2(0.0, 0.0);
+        for (int k = 0; k < kM2Warps; ++k) sum = cadd(sum, red[threadIdx.x][k]);
+        part[(size_t)threadIdx.x * BSE_MAX_VEC_BLOCKS + blockIdx.x] = sum;
+    }
+}
+
+inline int m2_blocks(int N) { return std::min((N + kM2Warps - 1) / kM2Warps, BSE_MAX_VEC_BLOCKS); }
+
 inline int vec_blocks(long long N) {
     long long b = (N + BSE_VEC_THREADS - 1) / BSE_VEC_THREADS;
     return (int)std::min<long long>(std::max<long long>(b, 1), BSE_MAX_VEC_BLOCKS);
@@ -1332,6 +1381,7 @@ inline bool staged_bands(const bse_interp* s) {
 
 // Number of <psi, w> block partials one H application leaves in the dot buffer.
 inline int dot_blocks(const bse_interp* s) {
+    if (s->scheme == BSE_SCHEME_M2) return m2_blocks(s->N);
     if (!s->learned && staged_bands(s)) return std::min(s->co->nkc, kProlongMaxCtas);
     return vec_blocks(s->N);
 }
@@ -1508,6 +1558,14 @@ int apply_h_typed(bse_ctx* ctx, bse_interp* s, int nchains, const void* psi_v, v
     cudaStream_t st = ctx->stream;
     const V* psi = (const V*)psi_v;
     V* W = (V*)w_v;
+    if (s->scheme == BSE_SCHEME_M2) {
+        if constexpr (std::is_same<T, double>::value) {
+            Timer tm(ctx, prof, KC_KCAPPLY);
+            k_m2_apply<<<m2_blocks(s->N), 32 * kM2Warps, 0, st>>>((const double2*)s->d_H2, psi, s->N, nchains, W,
+                                                                 s->d_part_dot);
+        }
+        return BSE_OK;
+    }
     const bool m3 = s->scheme == BSE_SCHEME_M3;
     const bool xh = near_tc_active(s);
     void* X = m3 ? s->d_X : nullptr;
@@ -1787,8 +1845,9 @@ int run_chains_typed(bse_ctx* ctx, bse_interp* s, int nch, const double* pol_dir
     BSE_CUDA_TRY(ctx, cudaMemcpyAsync(s->d_dirs, pol_dirs, sizeof(double) * 3 * nch, cudaMemcpyHostToDevice, st));
     if (prof) for (int k = 0; k < KC_COUNT; ++k) { ctx->kt_ms[k] = 0; ctx->kt_n[k] = 0; }
     if (graph) {
-        const long long key[5] = {ctx->serial, nch, m, flags & (BSE_REORTH_CGS2 | BSE_USE_GRAPH), s->state_serial};
-        if (!s->graph || !std::equal(key, key + 5, s->graph_key)) {
+        const long long key[6] = {ctx->serial, nch, m, flags & (BSE_REORTH_CGS2 | BSE_USE_GRAPH), s->state_serial,
+                                  ctx->wait_cycles};
+        if (!s->graph || !std::equal(key, key + 6, s->graph_key)) {
             if (s->graph) cudaGraphExecDestroy(s->graph);
             s->graph = nullptr;
             cudaGraph_t g = nullptr;
@@ -1805,7 +1864,7 @@ int run_chains_typed(bse_ctx* ctx, bse_interp* s, int nch, const double* pol_dir
                 ctx->err = std::string("graph capture: ") + cudaGetErrorString(e);
                 return BSE_ERR_CUDA;
             }
-            std::copy(key, key + 5, s->graph_key);
+            std::copy(key, key + 6, s->graph_key);
         }
         BSE_CUDA_TRY(ctx, cudaGraphLaunch(s->graph, st));
     } else {
@@ -1896,7 +1955,7 @@ int bse_run_batch(bse_ctx* ctx, bse_interp* const* sys, int nsys, const int* npo
     cudaStream_t main_st = ctx->stream;
     std::vector<int> first(nsys);
     int rc = BSE_OK, off = 0;
-    std::vector<long long> key = {ctx->serial, m, flags, conv ? (long long)ctx->stop_every : 0};
+    std::vector<long long> key = {ctx->serial, m, flags, conv ? (long long)ctx->stop_every : 0, ctx->wait_cycles};
     for (int i = 0; i < nsys; ++i) {
         bse_interp* s = sys[i];
         rc = (s->vec_prec == BSE_PREC_F64) ? ensure_state<double>(ctx, s, m, reorth, conv ? ctx->stop_nw : 0)
@@ -2042,6 +2101,11 @@ int apply_scratch_typed(bse_ctx* ctx, const bse_interp* s, int nchains, const vo
     cudaStream_t st = ctx->stream;
     const V* psi = (const V*)psi_v;
     V* W = (V*)w_v;
+    if (s->scheme == BSE_SCHEME_M2) {
+        if constexpr (std::is_same<T, double>::value)
+            k_m2_apply<<<m2_blocks(s->N), 32 * kM2Warps, 0, st>>>((const double2*)s->d_H2, psi, s->N, nchains, W, sc.dot);
+        return BSE_OK;
+    }
     const bool m3 = s->scheme == BSE_SCHEME_M3;
     const bool xh = near_tc_active(s);
     void* X = m3 ? sc.X : nullptr;

@@ -117,6 +117,7 @@ struct bse_ctx {
     double kt_ms[KC_COUNT] = {0, 0, 0, 0, 0};
     long long kt_n[KC_COUNT] = {0, 0, 0, 0, 0};
     int sm_count = 0;
+    long long wait_cycles = 0;        // bounded-wait budget of the K_c apply pipeline (0: default)
     // stopping rule of BSE_STOP_CONVERGED runs (bse_set_stop_rule)
     int stop_set = 0, stop_every = 0, stop_nw = 0;
     double stop_tol = 0, stop_seps = 0, stop_eta = 0;
@@ -152,6 +153,8 @@ struct bse_interp {
     int n = 0, nd = 0, Ndiv = 0, nk = 0, N = 0, t = 0, nv = 0, nc = 0;
     int scheme = 0, nb1 = 0, vec_prec = 0;
     double width = 0;
+    // Method 2: the dense interpolated Hamiltonian, complex128 [N][N]
+    void* d_H2 = nullptr;
     // dense tables
     void* d_dE = nullptr;            // T [N]
     void* d_Dv = nullptr;            // V [nk][8][nv*nv]
@@ -224,7 +227,7 @@ struct bse_interp {
     int eps_nw = 0;
     // cached graph of the step loop (BSE_USE_GRAPH) and what it was captured for
     cudaGraphExec_t graph = nullptr;
-    long long graph_key[5] = {0, 0, 0, 0, 0};   // context serial, chains, steps, flags, state serial
+    long long graph_key[6] = {0, 0, 0, 0, 0, 0};   // context serial, chains, steps, flags, state serial, wait limit
     long long serial = 0;            // unique per handle (the batch graph key)
     long long state_serial = 0;      // bumped whenever buffers a captured graph uses are replaced
 };

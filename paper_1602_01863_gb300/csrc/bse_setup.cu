@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "bse_internal.cuh"
 
@@ -227,6 +228,92 @@ __global__ void k_build_kc(const double2* __restrict__ M, const double2* __restr
         kr[(size_t)i * ldk + j] = __double2bfloat16(kv.x);
         ki[(size_t)i * ldk + j] = __double2bfloat16(kv.y);
     }
+}
+
+// ---------------------------------------------------------------- Method 2
+// Dense interpolation matrix (Eq. interpwfn) F [N][Nc], complex128:
+// F[(kd, v, c), (k~_l, n1, n2)] += f(kd, l) d_v^{n1} conj(d_c^{n2}); one thread per row.
+__global__ void k_m2_F(const double2* __restrict__ Dv, const double2* __restrict__ Dc, int n, int nd, int nv, int nc,
+                       int nb1, int N, int Nc, double2* __restrict__ F) {
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= N) return;
+    const int t = nv * nc, kd = row / t, tr = row % t, v = tr / nc, c = tr % nc;
+    const int Ndiv = nd * nd * nd, ic = kd / Ndiv, js = kd % Ndiv;
+    const Int3 i = unflat3(ic, n);
+    double2* fr = F + (size_t)row * Nc;
+    for (int l = 0; l < 8; ++l) {
+        const double f = interp_weight(js, l, nd, nb1);
+        if (f == 0.0) continue;
+        const int cic = flat3(i.a + ((l >> 2) & 1), i.b + ((l >> 1) & 1), i.c + (l & 1), n);
+        const double2* dv = Dv + ((size_t)kd * 8 + l) * nv * nv;
+        const double2* dc = Dc + ((size_t)kd * 8 + l) * nc * nc;
+        for (int n1 = 0; n1 < nv; ++n1)
+            for (int n2 = 0; n2 < nc; ++n2) {
+                const double2 val = cscale(cmul(dv[n1 * nv + v], conjg(dc[n2 * nc + c])), f);
+                double2* dst = fr + (size_t)cic * t + n1 * nc + n2;
+                *dst = cadd(*dst, val);
+            }
+    }
+}
+
+// Head of Eq. diverg for every coarse pair and the remainder:
+//   A[(i, n1 n2), (j, n3 n4)] = alpha O^v_{n1 n3}(i, j) O^c_{n2 n4}(i, j),
+//   Kmod = K_c - A h_head(q_coarse(i - j)).
+__global__ void k_m2_heads(const double2* __restrict__ Uv, const double2* __restrict__ Uc,
+                           const double* __restrict__ hh, const double2* __restrict__ Kc, int n, int nv, int nc,
+                           double alpha, int Nc, double2* __restrict__ A, double2* __restrict__ Kmod) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)Nc * Nc) return;
+    const int t = nv * nc, i = (int)(e / Nc), j = (int)(e % Nc);
+    const int ic = i / t, jc = j / t, n1 = (i % t) / nc, n2 = (i % t) % nc, n3 = (j % t) / nc, n4 = (j % t) % nc;
+    double2 ov = make_double2(0.0, 0.0), oc = make_double2(0.0, 0.0);
+    for (int m = 0; m < nv; ++m)
+        ov = cadd(ov, cmul(Uv[((size_t)ic * nv + m) * nv + n1], conjg(Uv[((size_t)jc * nv + m) * nv + n3])));
+    for (int m = 0; m < nc; ++m)
+        oc = cadd(oc, cmul(conjg(Uc[((size_t)ic * nc + m) * nc + n2]), Uc[((size_t)jc * nc + m) * nc + n4]));
+    const double2 a = cscale(cmul(ov, oc), alpha);
+    const Int3 ia = unflat3(ic, n), ib = unflat3(jc, n);
+    const double hc = hh[flat3(ia.a - ib.a, ia.b - ib.b, ia.c - ib.c, n)];
+    A[e] = a;
+    Kmod[e] = csub(Kc[e], cscale(a, hc));
+}
+
+// C [M][Nn] = X [M][K] Y [K][Nn] (conj_y = 0) or X Y^H with Y [Nn][K] (conj_y = 1),
+// complex128, 16 x 16 tiles staged in shared memory.
+__global__ void k_m2_gemm(const double2* __restrict__ X, const double2* __restrict__ Y, int M, int Nn, int K,
+                          int conj_y, double2* __restrict__ C) {
+    __shared__ double2 xs[16][17], ys[16][17];
+    const int r = blockIdx.y * 16 + threadIdx.y, col = blockIdx.x * 16 + threadIdx.x;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        const int kx = k0 + threadIdx.x, ky = k0 + threadIdx.y;
+        xs[threadIdx.y][threadIdx.x] = (r < M && kx < K) ? X[(size_t)r * K + kx] : make_double2(0.0, 0.0);
+        const int yc = blockIdx.x * 16 + threadIdx.x;
+        double2 yv = make_double2(0.0, 0.0);
+        if (yc < Nn && ky < K) yv = conj_y ? conjg(Y[(size_t)yc * K + ky]) : Y[(size_t)ky * Nn + yc];
+        ys[threadIdx.y][threadIdx.x] = yv;
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) acc = cadd(acc, cmul(xs[threadIdx.y][kk], ys[kk][threadIdx.x]));
+        __syncthreads();
+    }
+    if (r < M && col < Nn) C[(size_t)r * Nn + col] = acc;
+}
+
+// H = diag(dE) + (HA h_head(q_dense) + H) / N_div in place (H holds F Kmod F^H).
+__global__ void k_m2_combine(const double2* __restrict__ HA, const double* __restrict__ hd, const double* __restrict__ dE,
+                             int n, int nd, int t, int N, double2* __restrict__ H) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)N * N) return;
+    const int i = (int)(e / N), j = (int)(e % N);
+    const int L = n * nd, Ndiv = nd * nd * nd;
+    const int ki = i / t, kj = j / t;
+    const Int3 ci = unflat3(ki / Ndiv, n), si = unflat3(ki % Ndiv, nd), cj = unflat3(kj / Ndiv, n), sj = unflat3(kj % Ndiv, nd);
+    const double h = hd[flat3((ci.a - cj.a) * nd + si.a - sj.a, (ci.b - cj.b) * nd + si.b - sj.b,
+                              (ci.c - cj.c) * nd + si.c - sj.c, L)];
+    double2 v = cscale(cadd(cscale(HA[e], h), H[e]), 1.0 / Ndiv);
+    if (i == j) v.x += dE[i];
+    H[e] = v;
 }
 
 // K_c given by the caller (complex128 [Nc][Nc]) converted to the storage precision.
@@ -504,6 +591,52 @@ int apply_dense_inputs(bse_ctx* ctx, bse_interp* s, const bse_dense_inputs* in) 
     return BSE_OK;
 }
 
+// Method 2 set-up (FP64): the dense interpolated Hamiltonian, built with
+// temporaries F, A, Kmod, F M and F A F^H that are freed again.
+int build_m2(bse_ctx* ctx, bse_interp* s) {
+    const bse_coarse* c = s->co;
+    cudaStream_t st = ctx->stream;
+    const int N = s->N, Nc = c->Nc, L = s->n * s->nd;
+    double2 *F = nullptr, *A = nullptr, *Km = nullptr, *T = nullptr, *HA = nullptr;
+    double *hh = nullptr, *hd = nullptr;
+    int rc = BSE_OK;
+    auto cleanup = [&]() { cudaFree(F); cudaFree(A); cudaFree(Km); cudaFree(T); cudaFree(HA); cudaFree(hh); cudaFree(hd); };
+    if ((rc = bse_alloc(ctx, &s->d_H2, sizeof(double2) * (size_t)N * N, "Method 2 Hamiltonian")) != BSE_OK ||
+        (rc = bse_alloc(ctx, (void**)&F, sizeof(double2) * (size_t)N * Nc, "M2 F")) != BSE_OK ||
+        (rc = bse_alloc(ctx, (void**)&A, sizeof(double2) * (size_t)Nc * Nc, "M2 head")) != BSE_OK ||
+        (rc = bse_alloc(ctx, (void**)&Km, sizeof(double2) * (size_t)Nc * Nc, "M2 remainder")) != BSE_OK ||
+        (rc = bse_alloc(ctx, (void**)&T, sizeof(double2) * (size_t)N * Nc, "M2 temporary")) != BSE_OK ||
+        (rc = bse_alloc(ctx, (void**)&HA, sizeof(double2) * (size_t)N * N, "M2 head part")) != BSE_OK ||
+        (rc = bse_alloc(ctx, (void**)&hh, sizeof(double) * c->nkc, "coarse head table")) != BSE_OK ||
+        (rc = bse_alloc(ctx, (void**)&hd, sizeof(double) * (size_t)L * L * L, "dense head table")) != BSE_OK) {
+        cleanup();
+        return rc;
+    }
+    cudaMemsetAsync(F, 0, sizeof(double2) * (size_t)N * Nc, st);
+    k_m2_F<<<blocks_for(N, 128), 128, 0, st>>>((const double2*)s->d_Dv, (const double2*)s->d_Dc, s->n, s->nd, s->nv,
+                                               s->nc, s->nb1, N, Nc, F);
+    k_shape_table<<<blocks_for(c->nkc, 128), 128, 0, st>>>(s->n, c->kappa, 27, 0, 0.0, 1, hh);
+    k_shape_table<<<blocks_for((long long)L * L * L, 128), 128, 0, st>>>(L, c->kappa, 27, 0, 0.0, 1, hd);
+    k_m2_heads<<<blocks_for((long long)Nc * Nc, 256), 256, 0, st>>>(c->d_Uv, c->d_Uc, hh, (const double2*)c->d_kc, s->n,
+                                                                   s->nv, s->nc, c->alpha, Nc, A, Km);
+    const dim3 b16(16, 16);
+    // H <- F Kmod F^H, HA <- F A F^H
+    k_m2_gemm<<<dim3(blocks_for(Nc, 16), blocks_for(N, 16)), b16, 0, st>>>(F, Km, N, Nc, Nc, 0, T);
+    k_m2_gemm<<<dim3(blocks_for(N, 16), blocks_for(N, 16)), b16, 0, st>>>(T, F, N, N, Nc, 1, (double2*)s->d_H2);
+    k_m2_gemm<<<dim3(blocks_for(Nc, 16), blocks_for(N, 16)), b16, 0, st>>>(F, A, N, Nc, Nc, 0, T);
+    k_m2_gemm<<<dim3(blocks_for(N, 16), blocks_for(N, 16)), b16, 0, st>>>(T, F, N, N, Nc, 1, HA);
+    k_m2_combine<<<blocks_for((long long)N * N, 256), 256, 0, st>>>(HA, hd, (const double*)s->d_dE, s->n, s->nd, s->t,
+                                                                    N, (double2*)s->d_H2);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cleanup();
+    if (e != cudaSuccess) {
+        ctx->err = std::string("Method 2 set-up: ") + cudaGetErrorString(e);
+        return BSE_ERR_CUDA;
+    }
+    return BSE_OK;
+}
+
 template <typename T>
 int setup_interp_typed(bse_ctx* ctx, bse_interp* s, const bse_dense_inputs* dense) {
     using V = typename Cx<T>::V;
@@ -541,6 +674,9 @@ int setup_interp_typed(bse_ctx* ctx, bse_interp* s, const bse_dense_inputs* dens
     TRY(bse_alloc(ctx, (void**)&s->d_part_dot, sizeof(double2) * nvec * BSE_MAX_VEC_BLOCKS, "dot partials"));
     TRY(bse_alloc(ctx, (void**)&s->d_part_nrm, sizeof(double) * nvec * BSE_MAX_VEC_BLOCKS, "norm partials"));
     TRY(bse_alloc(ctx, (void**)&s->d_stop, sizeof(int) * nvec, "stop flags"));
+    if (s->scheme == BSE_SCHEME_M2) {
+        if constexpr (std::is_same<T, double>::value) TRY(build_m2(ctx, s));
+    }
     if (s->scheme == BSE_SCHEME_M3) {
         TRY(bse_alloc(ctx, &s->d_X, sizeof(V) * nvec * nk * 8 * t, "restricted pieces X"));
         TRY(bse_alloc(ctx, &s->d_U, sizeof(V) * nvec * nk * 8 * t, "near-field pieces"));

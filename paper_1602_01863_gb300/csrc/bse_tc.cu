@@ -17,8 +17,9 @@
 //
 // Warp roles (192 threads): warp 0 TMA producer, warp 1 MMA issuer and TMEM
 // owner, warps 2-5 epilogue (TMEM lanes 32 (w % 4) .. + 31).  Every mbarrier
-// wait is bounded; on expiry the kernel raises bit 0 of the context status word,
-// drains its copies and MMAs (bounded), frees TMEM and returns.
+// wait is bounded (by the context's wait limit, default ~2 s); on expiry the
+// kernel raises bit 0 of the context status word, drains its copies and MMAs
+// (waits bounded by the default), frees TMEM and returns.
 #include <cuda.h>
 
 #include <algorithm>
@@ -69,11 +70,12 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait: true when the phase completed, false (and status raised) on expiry.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status) {
+// Bounded wait: true when the phase completed, false (and status raised) on
+// expiry after `limit` clock cycles.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status, long long limit = WAIT_CYCLES) {
     const long long t0 = clock64();
     while (!mbar_try(bar, parity)) {
-        if (clock64() - t0 > WAIT_CYCLES) {
+        if (clock64() - t0 > limit) {
             atomicOr(status, 1);
             return false;
         }
@@ -133,7 +135,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_apply(const __grid_constan
                                                            const __grid_constant__ CUtensorMap map_ki,
                                                            const __grid_constant__ CUtensorMap map_b, int kblocks_per_row,
                                                            long long total_blocks, int seg_max,
-                                                           float* __restrict__ part, int* __restrict__ status) {
+                                                           float* __restrict__ part, int* __restrict__ status,
+                                                           long long wait_cycles) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     __shared__ uint64_t bar_full[STAGES], bar_empty[STAGES], bar_acc_full[2], bar_acc_empty[2], bar_drain;
@@ -174,7 +177,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_apply(const __grid_constan
             bool ok = true;
             for (long long q = q0; q < q1 && ok; ++q, ++it) {
                 const int s = (int)(it % STAGES);
-                if (it >= STAGES) ok = mbar_wait(smem_u32(&bar_empty[s]), (uint32_t)(((it / STAGES) - 1) & 1), status);
+                if (it >= STAGES) ok = mbar_wait(smem_u32(&bar_empty[s]), (uint32_t)(((it / STAGES) - 1) & 1), status, wait_cycles);
                 if (!ok) break;
                 const int tile = (int)(q / KB), kb = (int)(q % KB);
                 unsigned char* st = smem + (size_t)s * STAGE_BYTES;
@@ -200,11 +203,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_apply(const __grid_constan
                 const bool last = (q + 1 == q1) || ((q + 1) % KB == 0);
                 const int ab = seg & 1;
                 if (first && seg >= 2) {
-                    ok = mbar_wait(smem_u32(&bar_acc_empty[ab]), (uint32_t)(((seg >> 1) - 1) & 1), status);
+                    ok = mbar_wait(smem_u32(&bar_acc_empty[ab]), (uint32_t)(((seg >> 1) - 1) & 1), status, wait_cycles);
                     if (!ok) break;
                 }
                 const int s = (int)(it % STAGES);
-                ok = mbar_wait(smem_u32(&bar_full[s]), (uint32_t)((it / STAGES) & 1), status);
+                ok = mbar_wait(smem_u32(&bar_full[s]), (uint32_t)((it / STAGES) & 1), status, wait_cycles);
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t st = smem_u32(smem + (size_t)s * STAGE_BYTES);
@@ -231,7 +234,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_apply(const __grid_constan
         const int row = quarter * 32 + lane;
         for (int j = 0; j < nseg; ++j) {
             const int ab = j & 1;
-            const bool ok = mbar_wait(smem_u32(&bar_acc_full[ab]), (uint32_t)((j >> 1) & 1), status);
+            const bool ok = mbar_wait(smem_u32(&bar_acc_full[ab]), (uint32_t)((j >> 1) & 1), status, wait_cycles);
             if (!__all_sync(0xffffffffu, ok)) break;       // warp-uniform: tcgen05.ld is warp-collective
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             float v[32];
@@ -412,7 +415,7 @@ int tune_ctas(bse_ctx* ctx, bse_interp* s, const CUtensorMap& mkr, const CUtenso
         cudaMemcpy(d_q, p.q0.data(), sizeof(long long) * p.q0.size(), cudaMemcpyHostToDevice);
         auto launch = [&]() {
             k_tc_apply<<<p.ctas, TC_THREADS, STAGES * STAGE_BYTES + 1024, ctx->stream>>>(
-                mkr, mki, mb, p.kblocks_per_row, p.total, p.seg_max, d_part, ctx->d_status);
+                mkr, mki, mb, p.kblocks_per_row, p.total, p.seg_max, d_part, ctx->d_status, WAIT_CYCLES);
             k_tc_reduce<<<(c->Nc + 127) / 128, 128, 0, ctx->stream>>>(d_part, d_tc, d_q, p.kblocks_per_row, p.seg_max,
                                                                      c->Nc, 1, (float2*)s->d_R);
         };
@@ -490,7 +493,8 @@ int bse_tc_apply(bse_ctx* ctx, bse_interp* s, int nchains) {
     const TcState* st = reinterpret_cast<const TcState*>(s->tc_state);
     const TcPlan& p = st->plan;
     k_tc_apply<<<p.ctas, TC_THREADS, STAGES * STAGE_BYTES + 1024, ctx->stream>>>(
-        st->map_kr, st->map_ki, st->map_b, p.kblocks_per_row, p.total, p.seg_max, s->d_part, ctx->d_status);
+        st->map_kr, st->map_ki, st->map_b, p.kblocks_per_row, p.total, p.seg_max, s->d_part, ctx->d_status,
+        ctx->wait_cycles > 0 ? ctx->wait_cycles : WAIT_CYCLES);
     k_tc_reduce<<<(c->Nc + 127) / 128, 128, 0, ctx->stream>>>(s->d_part, st->d_tile_cta, st->d_q0, p.kblocks_per_row,
                                                              p.seg_max, c->Nc, nchains, (float2*)s->d_R);
     return BSE_OK;
@@ -513,7 +517,8 @@ int bse_tc_apply_scratch(bse_ctx* ctx, const bse_interp* s, int nchains, __nv_bf
     int rc = make_map(ctx, &map_b, bop, c->ldk, BN, BN);
     if (rc != BSE_OK) return rc;
     k_tc_apply<<<p.ctas, TC_THREADS, STAGES * STAGE_BYTES + 1024, ctx->stream>>>(
-        st->map_kr, st->map_ki, map_b, p.kblocks_per_row, p.total, p.seg_max, part, ctx->d_status);
+        st->map_kr, st->map_ki, map_b, p.kblocks_per_row, p.total, p.seg_max, part, ctx->d_status,
+        ctx->wait_cycles > 0 ? ctx->wait_cycles : WAIT_CYCLES);
     k_tc_reduce<<<(c->Nc + 127) / 128, 128, 0, ctx->stream>>>(part, st->d_tile_cta, st->d_q0, p.kblocks_per_row,
                                                              p.seg_max, c->Nc, nchains, (float2*)R);
     return BSE_OK;

@@ -62,24 +62,39 @@ def test_single_system_size_m3(ctx, kc_prec, vec_prec, tol):
     co.free()
 
 
-def test_largest_size_m1_and_learned_run(ctx):
+def test_largest_size_m1_m3_rows_and_trained_learned_run(ctx):
     """Coarse 12^3, 4v x 6c, n_div 4 (N = 2654208, BF16 K_c of 41472^2 = 6.9 GB):
-    sampled rows of one M1 application against the oracle; then 3 chains with
-    the learned correction (radius 8 dense steps, t = 24 stencil on the 48^3
-    mesh) for 12 steps: finite, positive b, Im eps >= 0."""
+    sampled rows of one M1 application against the oracle; the Method-3 near
+    field (t = 24: the CUDA-core kernel) as H^{M3} x - H^{M1} x on the same
+    BF16 K_c against the oracle's pair-by-pair correction on rows that include
+    the zone wrap (1e-3 of the row's near field: FP32 rounding of two
+    applications); then the learned correction with a network trained on the
+    method's pairs (4v x 6c, coarse 4^3, n_div 4) for 500 steps x 3 chains:
+    finite, positive b, Im eps >= 0, training loss halved."""
+    import bench
     from paper_1602_01863_gb300 import bse
     s = synth.largest_system()
     co = ctx.bse_build_coarse(s.model, s.n_coarse, bse.PREC_BF16)
     it = ctx.bse_interp_setup(co, s.n_div, bse.SCHEME_M1, 1.0, bse.PREC_F32)
+    it3 = ctx.bse_interp_setup(co, s.n_div, bse.SCHEME_M3, 1.0, bse.PREC_F32)
     x = synth.random_vectors(32, (1, it.N))
     y = _apply(ctx, it, x)[0]
+    y3 = _apply(ctx, it3, x)[0]
     I = oi.Interp(s.model, s.n_coarse, s.n_div, build_dense_kc=False)
     rows = np.array([3, 50000, it.Nk - 5])
     _check_rows(I, x[0], y, rows, False, 5e-3)
-    d_in = 6 + 2 * it.t
-    mlp = ctx.bse_mlp_create(d_in, 4096, bse.mlp_flatten(ol.init_params(d_in, seed=7)))
+    nf_rows = np.array([0, 1, 63, 70000, it.Nk - 1])
+    nf = (y3 - y).reshape(I.Nk, I.t)[nf_rows]
+    ref = I.near_field_rows(x[0], nf_rows)
+    per_row = np.abs(nf - ref).max(axis=1) / np.abs(ref).max(axis=1)
+    print("largest system: near-field per-row error", per_row)
+    assert per_row.max() <= 1e-3
+    it3.free()
+    mlp, first, last = bench.train_network(ctx, bse, synth, 4, 6, blocks=256, steps=1500)
+    assert last < 0.5 * first
     ctx.bse_interp_set_learned(it, mlp, 8)
-    a, b, pn2, st, rc = ctx.bse_haydock_run([it], [3], s.pol_dirs, 12, bse.USE_GRAPH)
+    a, b, pn2, st, rc = ctx.bse_haydock_run([it], [3], s.pol_dirs, 500, bse.USE_GRAPH)
+    assert rc == 0 and np.all(st == 500)
     assert np.all(np.isfinite(a)) and np.all(b[:, 1:] > 0)
     eps = ctx.bse_spectrum(a, b, pn2, st, 1.0 / it.Nk, 0.1, synth.frequency_grid(2000))
     assert np.all(eps.imag > -1e-9 * np.abs(eps.imag).max())
