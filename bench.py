@@ -496,10 +496,13 @@ def cpu_model() -> str:
         txt = open("/proc/cpuinfo").read()
     except OSError:
         return "unknown"
+    arm_parts = {"0xd4f": "Arm Neoverse V2", "0xd40": "Arm Neoverse V1", "0xd0c": "Arm Neoverse N1",
+                 "0xd49": "Arm Neoverse N2", "0xd83": "Arm Neoverse V3"}
     for key in ("model name", "Model Name", "CPU part"):
         for line in txt.splitlines():
             if line.split(":")[0].strip() == key:
-                return f"{key}: {line.split(':', 1)[1].strip()}"
+                val = line.split(":", 1)[1].strip()
+                return arm_parts.get(val, f"{key}: {val}") if key == "CPU part" else val
     return "unknown"
 
 
