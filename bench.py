@@ -328,7 +328,7 @@ def run_ours(args):
         cpu = cpu_baseline(rows=24)
 
 
-    launches_per_step = 1 + 2 + 1 + 1 + 4          # restrict, tc apply + reduce, near field, prolong, 4 Lanczos
+    launches_per_step = 1 + 1 + 1 + 1 + 2          # restrict, tc apply, near field, prolong, 2 Lanczos
     launches = args.steps * (m * launches_per_step + 3 + 1)
     if rank == 0:
         line = {

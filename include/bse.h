@@ -198,6 +198,13 @@ void bse_free_interp(bse_interp* interp);
  * [6] = number of near offsets (M3, else 0), [7] = vec_prec. */
 int bse_interp_info(const bse_interp* interp, long long* info);
 
+/* Launch shape the set-up's autotuner chose for the tensor-core K_c apply
+ * (BF16 K_c only; Eq. matmul2): plan[0] = pipeline stages (TMA ring depth),
+ * plan[1] = k-blocks of 64 columns per work chunk, plan[2] = CTAs.
+ * Host array `plan` [3], written on success.  Errors: BSE_ERR_ARG (NULL),
+ * BSE_ERR_UNSUPPORTED (K_c not BF16). */
+int bse_interp_kc_plan(const bse_interp* interp, int* plan);
+
 /* Dipole start vectors P(e) = sum_alpha e_alpha P^alpha for `npol`
  * directions (host [npol][3]) into device `p_out` [npol][N] in the interp's
  * vector precision, and their squared norms (FP64) into host `pnorm2` [npol]. */

@@ -36,7 +36,7 @@ EXPORTED = ("bse_version", "bse_ctx_create", "bse_ctx_destroy", "bse_last_error"
             "bse_dipoles", "bse_apply_h", "bse_apply_h_noalloc", "bse_haydock_run", "bse_last_kernel_times",
             "bse_spectrum", "bse_mlp_param_count", "bse_mlp_create", "bse_mlp_free", "bse_mlp_get_params",
             "bse_mlp_forward", "bse_mlp_gradients", "bse_mlp_train_step", "bse_pairs_generate",
-            "bse_interp_set_learned", "bse_set_stop_rule", "bse_ctx_set_wait_limit")
+            "bse_interp_set_learned", "bse_set_stop_rule", "bse_ctx_set_wait_limit", "bse_interp_kc_plan")
 
 
 class BseError(RuntimeError):
@@ -93,6 +93,7 @@ def load(path: str | None = None):
     lib.bse_free_interp.argtypes = [_P]
     lib.bse_free_interp.restype = None
     lib.bse_interp_info.argtypes = [_P, C.POINTER(C.c_longlong)]
+    lib.bse_interp_kc_plan.argtypes = [_P, _I]
     lib.bse_dipoles.argtypes = [_P, _P, C.c_int, _D, _P, _D]
     lib.bse_apply_h.argtypes = [_P, _P, C.c_int, _P, _P]
     lib.bse_apply_h_noalloc.argtypes = [_P, _P, C.c_int, _P, _P]
@@ -161,6 +162,15 @@ class Interp:
         info = (C.c_longlong * 8)()
         ctx._check(ctx.lib.bse_interp_info(handle, info))
         self.N, self.Nk, self.Nc, self.t, self.n, self.n_div, self.n_near, self.vec_prec = [int(x) for x in info]
+
+    def kc_plan(self):
+        """(pipeline stages, k-blocks per chunk, CTAs) of the tensor-core K_c apply, or None (K_c not BF16)."""
+        plan = (C.c_int * 3)()
+        rc = self.ctx.lib.bse_interp_kc_plan(self.handle, plan)
+        if rc == BSE_ERR_UNSUPPORTED:
+            return None
+        self.ctx._check(rc)
+        return tuple(int(x) for x in plan)
 
     def free(self):
         if self.handle:

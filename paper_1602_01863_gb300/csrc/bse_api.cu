@@ -92,7 +92,8 @@ int bse_ctx_create(bse_ctx** out, int device, void* cuda_stream) {
     // Load the library's device module and look up the no-allocation scratch
     // here, at set-up, so that bse_apply_h_noalloc never triggers the lazy
     // module load (and its allocation) itself.
-    if (bse_noalloc_prepare(ctx) != BSE_OK) {
+    if (bse_noalloc_prepare(ctx) != BSE_OK || bse_prepare_aux(ctx) != BSE_OK) {
+        bse_release_ctx_state(ctx);
         cudaFree(ctx->d_status);
         if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
         delete ctx;
@@ -243,6 +244,13 @@ int bse_interp_info(const bse_interp* s, long long* info) {
     if (!s || !info) return BSE_ERR_ARG;
     info[0] = s->N; info[1] = s->nk; info[2] = s->co->Nc; info[3] = s->t;
     info[4] = s->n; info[5] = s->nd; info[6] = s->n_near; info[7] = s->vec_prec;
+    return BSE_OK;
+}
+
+int bse_interp_kc_plan(const bse_interp* s, int* plan) {
+    if (!s || !plan) return BSE_ERR_ARG;
+    if (!s->tc_state) return BSE_ERR_UNSUPPORTED;
+    plan[0] = s->tc_stages; plan[1] = s->tc_kblocks; plan[2] = s->tc_ctas;
     return BSE_OK;
 }
 

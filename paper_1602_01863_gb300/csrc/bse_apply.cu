@@ -1181,14 +1181,125 @@ __global__ void __launch_bounds__(256) k_lanczos_axpy4(float4* __restrict__ W, c
     }
 }
 
+// One launch for a_i, the update and b_{i+1} (FP32 vectors, no
+// reorthogonalisation; 256 threads per block, grid-stride).  GB300 issues FP64
+// at a small fraction of its FP32 rate, so the FP64 work here is per block or
+// per warp, never per element:
+//  * a_i: warp 0 of every block sums the <psi, w> block partials of the H
+//    application in FP64, in the same fixed order in every block (block 0
+//    stores a_i and its imaginary part);
+//  * the update and ||w||^2 in FP32 per thread and per warp (shuffles), the 8
+//    warp sums of a block in FP64 into its partial;
+//  * the last block to finish (a counter that it resets) sums the block
+//    partials in FP64 in a fixed order into b_{i+1} and applies the breakdown
+//    test b_{i+1} < 1e-12 max_j |a_j|.
+template <int NCH>
+__global__ void __launch_bounds__(256) k_lanczos_axpy4_ab(float4* __restrict__ W, const float4* __restrict__ psi,
+                                                          const float4* __restrict__ psi_prev,
+                                                          const double2* __restrict__ dot, int ndot, double* __restrict__ a,
+                                                          double* __restrict__ aim, double* __restrict__ b, int step, int m,
+                                                          int N4, double* __restrict__ part,
+                                                          int* __restrict__ stop, int* __restrict__ ctr) {
+    __shared__ float wsum[NCH][8];
+    __shared__ double a_sh[NCH];
+    __shared__ float ab_sh[NCH][2];
+    __shared__ int run_sh[NCH];
+    __shared__ int last_sh;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0) {
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) {
+            const int run = stop[ch] == 0;                 // uniform over the grid until the last block
+            double2 s = make_double2(0.0, 0.0);
+            if (run)
+                for (int i = lane; i < ndot; i += 32) s = cadd(s, dot[(size_t)ch * BSE_MAX_VEC_BLOCKS + i]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                s.x += __shfl_down_sync(0xffffffffu, s.x, o);
+                s.y += __shfl_down_sync(0xffffffffu, s.y, o);
+            }
+            if (lane == 0) {
+                run_sh[ch] = run;
+                a_sh[ch] = s.x;
+                ab_sh[ch][0] = (float)s.x;
+                ab_sh[ch][1] = (float)b[ch * (m + 1) + step];
+                if (blockIdx.x == 0 && run) {
+                    a[ch * m + step] = s.x;
+                    aim[ch * m + step] = s.y;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    float nrm[NCH];
+#pragma unroll
+    for (int ch = 0; ch < NCH; ++ch) {
+        nrm[ch] = 0.f;
+        if (!run_sh[ch]) continue;
+        const float ai = ab_sh[ch][0], bi = ab_sh[ch][1];
+        for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < N4; g += gridDim.x * blockDim.x) {
+            const size_t o = (size_t)ch * N4 + g;
+            const float4 w = W[o], p = psi[o], q = psi_prev[o];
+            float4 r;
+            r.x = fmaf(-bi, q.x, fmaf(-ai, p.x, w.x));
+            r.y = fmaf(-bi, q.y, fmaf(-ai, p.y, w.y));
+            r.z = fmaf(-bi, q.z, fmaf(-ai, p.z, w.z));
+            r.w = fmaf(-bi, q.w, fmaf(-ai, p.w, w.w));
+            W[o] = r;
+            nrm[ch] = fmaf(r.x, r.x, fmaf(r.y, r.y, fmaf(r.z, r.z, fmaf(r.w, r.w, nrm[ch]))));
+        }
+    }
+#pragma unroll
+    for (int ch = 0; ch < NCH; ++ch) {
+        float x = nrm[ch];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) wsum[ch][warp] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < NCH && run_sh[threadIdx.x]) {
+        double s = 0.0;
+        for (int w = 0; w < 8; ++w) s += (double)wsum[threadIdx.x][w];
+        part[(size_t)threadIdx.x * BSE_MAX_VEC_BLOCKS + blockIdx.x] = s;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last_sh = atomicAdd(ctr, 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (!last_sh || warp != 0) return;
+    __threadfence();
+#pragma unroll
+    for (int ch = 0; ch < NCH; ++ch) {
+        if (!run_sh[ch]) continue;
+        double s = 0.0, am = lane == 0 ? fabs(a_sh[ch]) : 0.0;
+        for (int i = lane; i < (int)gridDim.x; i += 32) s += __ldcg(part + (size_t)ch * BSE_MAX_VEC_BLOCKS + i);
+        for (int j = lane; j < step; j += 32) am = fmax(am, fabs(a[ch * m + j]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s += __shfl_down_sync(0xffffffffu, s, o);
+            am = fmax(am, __shfl_down_sync(0xffffffffu, am, o));
+        }
+        if (lane == 0) {
+            const double bn = sqrt(s);
+            b[ch * (m + 1) + step + 1] = bn;
+            if (!(bn >= 1e-12 * am)) stop[ch] = step + 1;
+        }
+    }
+    if (lane == 0) *ctr = 0;
+}
+
 // psi_{i+1} = w / b_{i+1} (written over psi_{i-1}), also into the basis when kept.
 __global__ void __launch_bounds__(256) k_lanczos_scale4(const float4* __restrict__ W, float4* __restrict__ out,
                                                         const double* __restrict__ b, int step, int m, int N4,
                                                         int nchains, float4* __restrict__ basis, int mb,
                                                         const int* __restrict__ stop) {
+    // 1 / b_{i+1} once per block (FP64 is slow per element on GB300)
+    __shared__ float inv_sh[BSE_MAX_CHAINS];
+    if (threadIdx.x < nchains) inv_sh[threadIdx.x] = (float)(1.0 / b[threadIdx.x * (m + 1) + step + 1]);
+    __syncthreads();
     for (int ch = 0; ch < nchains; ++ch) {
         if (stop[ch]) continue;
-        const float inv = (float)(1.0 / b[ch * (m + 1) + step + 1]);
+        const float inv = inv_sh[ch];
         for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < N4; g += gridDim.x * blockDim.x) {
             const float4 w = W[(size_t)ch * N4 + g];
             const float4 v = make_float4(w.x * inv, w.y * inv, w.z * inv, w.w * inv);
@@ -1204,15 +1315,21 @@ __global__ void k_reduce_b(const double* __restrict__ part, int nblk, int step, 
     __shared__ double2 sh[256];
     const int ch = blockIdx.x;
     if (stop[ch]) return;
-    double s = 0.0;
+    double s = 0.0, am = 0.0;
     for (int i = threadIdx.x; i < nblk; i += blockDim.x) s += part[(size_t)ch * BSE_MAX_VEC_BLOCKS + i];
+    for (int j = threadIdx.x; j <= step; j += blockDim.x) am = fmax(am, fabs(a[ch * m + j]));
     const double2 r = block_sum2(make_double2(s, 0.0), sh);
+    // block maximum of |a_j| (the second component of sh is free)
+    sh[threadIdx.x].y = am;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x].y = fmax(sh[threadIdx.x].y, sh[threadIdx.x + o].y);
+        __syncthreads();
+    }
     if (threadIdx.x == 0) {
         const double bn = sqrt(r.x);
         b[ch * (m + 1) + step + 1] = bn;
-        double amax = 0.0;
-        for (int j = 0; j <= step; ++j) amax = fmax(amax, fabs(a[ch * m + j]));
-        if (!(bn >= 1e-12 * amax)) stop[ch] = step + 1;
+        if (!(bn >= 1e-12 * sh[0].y)) stop[ch] = step + 1;
     }
 }
 
@@ -1576,19 +1693,36 @@ int apply_h_typed(bse_ctx* ctx, bse_interp* s, int nchains, const void* psi_v, v
         Timer tm(ctx, prof, KC_RESTRICT);
         launch_restrict<T>(ctx, s, nchains, psi, s->d_Q, s->d_Bop, X, xh, xscale, s->d_U);
     }
-    {
-        Timer tm(ctx, prof, KC_KCAPPLY);
-        if (c->kc_prec == BSE_PREC_BF16) {
-            int rc = bse_tc_apply(ctx, s, nchains);
-            if (rc != BSE_OK) return rc;
-        } else {
-            k_kc_apply_simt<T><<<(c->Nc + 7) / 8, 256, 0, st>>>((const V*)c->d_kc, (const V*)s->d_Q, c->Nc, nchains, (V*)s->d_R);
-        }
-    }
-    if (m3) {
-        Timer tm(ctx, prof, KC_NEAR);
-        int rc = bse_launch_near_field(ctx, s, nchains, X, xscale, s->d_U);
+    // The K_c apply and the near field read only what restrict wrote.  With the
+    // tensor-core near field (one CTA per coarse cell, so its last wave leaves
+    // SMs idle) the apply runs on the lane's auxiliary stream at the lowest
+    // scheduling priority and the near field at the highest: the apply's CTAs
+    // take SMs only once every near-field CTA has one, and share the chunks of
+    // K_c among themselves.  Profiled runs keep the kernels one after another.
+    const int ln = ctx->lane;
+    if (xh && c->kc_prec == BSE_PREC_BF16 && !prof && ctx->aux[ln]) {
+        BSE_CUDA_TRY(ctx, cudaEventRecord(ctx->aux_fork[ln], st));
+        BSE_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->aux[ln], ctx->aux_fork[ln], 0));
+        int rc = bse_near_tc_launch(ctx, s, nchains, X, xscale, s->d_U, true, ctx->prio_greatest);
         if (rc != BSE_OK) return rc;
+        if ((rc = bse_tc_apply(ctx, s, nchains, ctx->aux[ln], true, ctx->prio_least)) != BSE_OK) return rc;
+        BSE_CUDA_TRY(ctx, cudaEventRecord(ctx->aux_join[ln], ctx->aux[ln]));
+        BSE_CUDA_TRY(ctx, cudaStreamWaitEvent(st, ctx->aux_join[ln], 0));
+    } else {
+        {
+            Timer tm(ctx, prof, KC_KCAPPLY);
+            if (c->kc_prec == BSE_PREC_BF16) {
+                int rc = bse_tc_apply(ctx, s, nchains, st, false, 0);
+                if (rc != BSE_OK) return rc;
+            } else {
+                k_kc_apply_simt<T><<<(c->Nc + 7) / 8, 256, 0, st>>>((const V*)c->d_kc, (const V*)s->d_Q, c->Nc, nchains, (V*)s->d_R);
+            }
+        }
+        if (m3) {
+            Timer tm(ctx, prof, KC_NEAR);
+            int rc = bse_launch_near_field(ctx, s, nchains, X, xscale, s->d_U);
+            if (rc != BSE_OK) return rc;
+        }
     }
     {
         Timer tm(ctx, prof, KC_PROLONG);
@@ -1689,6 +1823,8 @@ int ensure_state(bse_ctx* ctx, bse_interp* s, int m, bool reorth, int nw) {
     if (!s->d_dirs) {
         if ((rc = bse_alloc(ctx, (void**)&s->d_dirs, sizeof(double) * 3 * BSE_MAX_CHAINS, "directions")) != BSE_OK) return rc;
         if ((rc = bse_alloc(ctx, (void**)&s->d_pn2, sizeof(double) * BSE_MAX_CHAINS, "norms")) != BSE_OK) return rc;
+        if ((rc = bse_alloc(ctx, (void**)&s->d_lz_ctr, sizeof(int), "Lanczos counter")) != BSE_OK) return rc;
+        BSE_CUDA_TRY(ctx, cudaMemset(s->d_lz_ctr, 0, sizeof(int)));
     }
     if (s->m_alloc < m) {
         drop_graph(s);
@@ -1751,6 +1887,19 @@ int enqueue_chains(bse_ctx* ctx, bse_interp* s, int nch, int m, bool reorth, boo
         int rc = apply_h_typed<T>(ctx, s, nch, B, W, prof, true);
         if (rc != BSE_OK) return rc;
         Timer tm(ctx, prof, KC_LANCZOS);
+        if (vec4 && !reorth) {
+            // a_i, the update and b_{i+1} in one launch, then the scale
+#define BSE_AXPY_AB(NCH_)                                                                                       \
+    k_lanczos_axpy4_ab<NCH_><<<nbab, 256, 0, st>>>((float4*)W, (const float4*)B, (const float4*)A, s->d_part_dot,    \
+                                                  dot_blocks(s), s->d_a, s->d_aim, s->d_b, i, m, N / 2, s->d_part_nrm, \
+                                                  s->d_stop, s->d_lz_ctr)
+            const int nbab = std::min(nb4, 4 * std::max(ctx->sm_count, 1));
+            if (nch == 1) BSE_AXPY_AB(1);
+            else if (nch == 2) BSE_AXPY_AB(2);
+            else if (nch == 3) BSE_AXPY_AB(3);
+            else BSE_AXPY_AB(4);
+#undef BSE_AXPY_AB
+        } else {
         k_reduce_a<<<nch, 256, 0, st>>>(s->d_part_dot, dot_blocks(s), i, m, s->d_a, s->d_aim, s->d_stop);
         if (vec4)
             k_lanczos_axpy4<<<nb4, 256, 0, st>>>((float4*)W, (const float4*)B, (const float4*)A, s->d_a, s->d_b, i, m,
@@ -1766,7 +1915,8 @@ int enqueue_chains(bse_ctx* ctx, bse_interp* s, int nch, int m, bool reorth, boo
                     k_cgs_update<T><<<nb, BSE_VEC_THREADS, 0, st>>>(basis, W, s->d_cgs_h, i + 1, mb, N, ch, s->d_part_nrm);
                 }
         }
-        k_reduce_b<<<nch, 256, 0, st>>>(s->d_part_nrm, (vec4 && !reorth) ? nb4 : nb, i, m, s->d_a, s->d_b, s->d_stop);
+        k_reduce_b<<<nch, 256, 0, st>>>(s->d_part_nrm, nb, i, m, s->d_a, s->d_b, s->d_stop);
+        }
         if (rule && (i + 1) % rule->every == 0) {
             const int nblk = (rule->nw + kConvThreads - 1) / kConvThreads;
             k_conv_eval<<<dim3(nblk, nch), kConvThreads, 0, st>>>(s->d_a, s->d_b, i + 1, m, s->d_pn2, rule->pref, rule->eta,
@@ -1856,7 +2006,7 @@ int run_chains_typed(bse_ctx* ctx, bse_interp* s, int nch, const double* pol_dir
                 rc = enqueue_chains<T>(ctx, s, nch, m, reorth, false, nullptr, false);
                 e = cudaStreamEndCapture(st, &g);
             }
-            if (e == cudaSuccess && rc == BSE_OK) e = cudaGraphInstantiate(&s->graph, g, 0);
+            if (e == cudaSuccess && rc == BSE_OK) e = cudaGraphInstantiate(&s->graph, g, cudaGraphInstantiateFlagUseNodePriority);
             if (g) cudaGraphDestroy(g);
             if (rc != BSE_OK) return rc;
             if (e != cudaSuccess) {
@@ -1900,8 +2050,8 @@ int dipoles_typed(bse_ctx* ctx, bse_interp* s, int npol, const double* pol_dirs,
 void bse_release_run_state(bse_interp* s) {
     if (s->graph) cudaGraphExecDestroy(s->graph);
     s->graph = nullptr;
-    cudaFree(s->d_dirs); cudaFree(s->d_pn2); cudaFree(s->d_eps_prev); cudaFree(s->d_conv_part);
-    s->d_dirs = nullptr; s->d_pn2 = nullptr; s->d_eps_prev = nullptr; s->d_conv_part = nullptr;
+    cudaFree(s->d_dirs); cudaFree(s->d_pn2); cudaFree(s->d_eps_prev); cudaFree(s->d_conv_part); cudaFree(s->d_lz_ctr);
+    s->d_dirs = nullptr; s->d_pn2 = nullptr; s->d_eps_prev = nullptr; s->d_conv_part = nullptr; s->d_lz_ctr = nullptr;
 }
 
 void bse_release_ctx_state(bse_ctx* ctx) {
@@ -1915,6 +2065,14 @@ void bse_release_ctx_state(bse_ctx* ctx) {
     }
     if (ctx->side_fork) cudaEventDestroy(ctx->side_fork);
     ctx->side_fork = nullptr;
+    for (int k = 0; k < 9; ++k) {
+        if (ctx->aux[k]) cudaStreamDestroy(ctx->aux[k]);
+        if (ctx->aux_fork[k]) cudaEventDestroy(ctx->aux_fork[k]);
+        if (ctx->aux_join[k]) cudaEventDestroy(ctx->aux_join[k]);
+        ctx->aux[k] = nullptr;
+        ctx->aux_fork[k] = nullptr;
+        ctx->aux_join[k] = nullptr;
+    }
     cudaFree(ctx->cf_buf);
     ctx->cf_buf = nullptr;
     ctx->cf_bytes = 0;
@@ -1923,6 +2081,18 @@ void bse_release_ctx_state(bse_ctx* ctx) {
 }
 
 void bse_invalidate_graph(bse_interp* s) { drop_graph(s); }
+
+// Auxiliary streams (lowest priority, non-blocking) and fork / join events of
+// the concurrent K_c apply, one set per lane; created with the context.
+int bse_prepare_aux(bse_ctx* ctx) {
+    BSE_CUDA_TRY(ctx, cudaDeviceGetStreamPriorityRange(&ctx->prio_least, &ctx->prio_greatest));
+    for (int k = 0; k < 9; ++k) {
+        BSE_CUDA_TRY(ctx, cudaStreamCreateWithPriority(&ctx->aux[k], cudaStreamNonBlocking, ctx->prio_least));
+        BSE_CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->aux_fork[k], cudaEventDisableTiming));
+        BSE_CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->aux_join[k], cudaEventDisableTiming));
+    }
+    return BSE_OK;
+}
 
 int bse_apply_once(bse_ctx* ctx, bse_interp* s, int nvec, const void* x, void* y, bool profile) {
     int rc = (s->vec_prec == BSE_PREC_F64) ? apply_h_typed<double>(ctx, s, nvec, x, y, profile, false)
@@ -2010,12 +2180,14 @@ int bse_run_batch(bse_ctx* ctx, bse_interp* const* sys, int nsys, const int* npo
                 const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
                 load[k] += cost[i];
                 ctx->stream = ctx->side[k];
+                ctx->lane = 1 + k;
                 StopRule rule{};
                 if (conv) rule = stop_rule_for(ctx, sys[i]);
                 rc = (sys[i]->vec_prec == BSE_PREC_F64)
                          ? enqueue_chains<double>(ctx, sys[i], npol[i], m, reorth, false, conv ? &rule : nullptr, false)
                          : enqueue_chains<float>(ctx, sys[i], npol[i], m, reorth, false, conv ? &rule : nullptr, false);
                 ctx->stream = main_st;
+                ctx->lane = 0;
                 if (rc != BSE_OK) break;
             }
             for (int k = 0; k < K; ++k) {
@@ -2025,7 +2197,8 @@ int bse_run_batch(bse_ctx* ctx, bse_interp* const* sys, int nsys, const int* npo
             e = cudaStreamEndCapture(main_st, &g);
         }
         ctx->stream = main_st;
-        if (e == cudaSuccess && rc == BSE_OK) e = cudaGraphInstantiate(&ctx->batch_graph, g, 0);
+        ctx->lane = 0;
+        if (e == cudaSuccess && rc == BSE_OK) e = cudaGraphInstantiate(&ctx->batch_graph, g, cudaGraphInstantiateFlagUseNodePriority);
         if (g) cudaGraphDestroy(g);
         if (rc != BSE_OK) return rc;
         if (e != cudaSuccess) {

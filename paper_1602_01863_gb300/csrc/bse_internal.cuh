@@ -131,6 +131,14 @@ struct bse_ctx {
     cudaEvent_t side_fork = nullptr;
     cudaGraphExec_t batch_graph = nullptr;
     std::vector<long long> batch_key;   // serials of the systems, npol, steps, flags
+    // Concurrent K_c apply beside the near field: one auxiliary stream and a
+    // fork / join event pair per lane (0: the context stream, 1 + k: batch side
+    // stream k); `lane` is the lane whose stream ctx->stream currently is.
+    cudaStream_t aux[9] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t aux_fork[9] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t aux_join[9] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    int lane = 0;
+    int prio_least = 0, prio_greatest = 0;   // stream priority range of the device
 };
 
 struct bse_coarse {
@@ -197,8 +205,9 @@ struct bse_interp {
     void* d_X = nullptr;             // V [4][nk][8][t]
     void* d_U = nullptr;             // V [4][nk][8][t]
     __nv_bfloat16* d_Bop = nullptr;  // [16][ldk] split-BF16 operand of the tensor-core apply
-    float* d_part = nullptr;         // split-K partial sums of the tensor-core apply
-    int tc_ctas = 0, tc_kblocks = 0; // tensor-core schedule
+    float* d_part = nullptr;         // chunk partials + counters of the tensor-core apply
+    int tc_ctas = 0, tc_kblocks = 0; // tensor-core schedule: CTAs, k-blocks per chunk
+    int tc_stages = 0;               // and pipeline depth (autotuned)
     void* tc_state = nullptr;        // tensor maps + schedule tables (bse_tc.cu)
     void* d_vec[3] = {nullptr, nullptr, nullptr};   // V [4][N]: psi_A, psi_B, w
     double2* d_part_dot = nullptr;   // [4][BSE_MAX_VEC_BLOCKS] FP64 block partials
@@ -222,6 +231,7 @@ struct bse_interp {
     // per-run buffers (kept: no allocation inside a run once they exist)
     double* d_dirs = nullptr;        // [4][3] polarisation directions
     double* d_pn2 = nullptr;         // [4]    ||P||^2
+    int* d_lz_ctr = nullptr;         // finished-block counter of k_lanczos_axpy4_ab (zero between launches)
     double2* d_eps_prev = nullptr;   // [4][eps_nw] spectrum at the previous convergence check
     double* d_conv_part = nullptr;   // [4][eps_nblk][4] block maxima of a convergence check
     int eps_nw = 0;
@@ -268,6 +278,7 @@ int bse_run_chains(bse_ctx* ctx, bse_interp* s, int npol, const double* pol_dirs
 void bse_release_run_state(bse_interp* s);
 void bse_invalidate_graph(bse_interp* s);   // a cached step-loop graph no longer matches the handle
 void bse_release_ctx_state(bse_ctx* ctx);
+int bse_prepare_aux(bse_ctx* ctx);          // auxiliary streams of the concurrent K_c apply
 int bse_run_batch(bse_ctx* ctx, bse_interp* const* sys, int nsys, const int* npol, const double* pol_dirs, int m,
                   int flags, double* a, double* b, double* pnorm2, int* steps_done);
 int bse_make_dipoles(bse_ctx* ctx, bse_interp* s, int npol, const double* pol_dirs, void* p_out,
@@ -278,7 +289,9 @@ int bse_cf_device(bse_ctx* ctx, int nchains, int nsteps, const int* steps_done, 
 
 // tensor-core K_c apply (bse_tc.cu)
 int bse_tc_prepare(bse_ctx* ctx, bse_interp* s);
-int bse_tc_apply(bse_ctx* ctx, bse_interp* s, int nchains);
+// prio: launch with scheduling priority prio_value (used when the apply runs
+// beside the near field on an auxiliary stream).
+int bse_tc_apply(bse_ctx* ctx, bse_interp* s, int nchains, cudaStream_t stream, bool prio, int prio_value);
 void bse_tc_release(bse_interp* s);
 
 // Per-call scratch of one H application, supplied by the caller instead of the
@@ -295,7 +308,8 @@ struct ApplyScratch {
 int bse_launch_near_field(bse_ctx* ctx, const bse_interp* s, int nchains, const void* X, const float* xscale, void* U);
 int bse_apply_learned(bse_ctx* ctx, const bse_interp* s, int nchains, const void* psi, void* w, double2* dot);
 int bse_near_tc_prepare(bse_ctx* ctx, bse_interp* s, const std::vector<std::vector<NearEntry>>& per_slot);
-int bse_near_tc_launch(bse_ctx* ctx, const bse_interp* s, int nchains, const void* Xh, const float* xscale, void* U);
+int bse_near_tc_launch(bse_ctx* ctx, const bse_interp* s, int nchains, const void* Xh, const float* xscale, void* U,
+                       bool prio = false, int prio_value = 0);
 float bse_near_tc_xscale(const bse_interp* s, double norm);
 size_t bse_tc_part_bytes(const bse_interp* s);
 int bse_tc_apply_scratch(bse_ctx* ctx, const bse_interp* s, int nchains, __nv_bfloat16* bop, float* part, void* R);

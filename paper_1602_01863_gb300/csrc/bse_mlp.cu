@@ -14,6 +14,7 @@
 #include <cmath>
 #include <vector>
 
+#include "bse_dmat.cuh"
 #include "bse_internal.cuh"
 
 namespace {
@@ -226,8 +227,6 @@ int mlp_grads(bse_ctx* ctx, bse_mlp* m, int B, const float* X, const float* Y, d
 // ================================================ pair data from the method
 namespace {
 
-__device__ void dmat_expm_i(const double2* A, int n, double2* E);   // defined below
-
 // Band gauge at integer grid point g (L points per axis) from the generators.
 __device__ void gauge_at(const double2* gen, int nb, const int g[3], int L, double2* U) {
     double2 A[BSE_MAX_BANDS * BSE_MAX_BANDS];
@@ -240,41 +239,6 @@ __device__ void gauge_at(const double2* gen, int nb, const int g[3], int L, doub
         for (int i = 0; i < nb * nb; ++i) A[i] = cadd(A[i], cadd(cscale(g0[i], s), cscale(g1[i], 1.0 - c)));
     }
     dmat_expm_i(A, nb, U);
-}
-
-__device__ void dmat_mul(const double2* A, const double2* B, double2* C, int n) {
-    for (int i = 0; i < n; ++i)
-        for (int j = 0; j < n; ++j) {
-            double2 s = make_double2(0.0, 0.0);
-            for (int k = 0; k < n; ++k) s = cadd(s, cmul(A[i * n + k], B[k * n + j]));
-            C[i * n + j] = s;
-        }
-}
-
-__device__ void dmat_expm_i(const double2* A, int n, double2* E) {
-    double fro = 0.0;
-    for (int i = 0; i < n * n; ++i) fro += A[i].x * A[i].x + A[i].y * A[i].y;
-    fro = sqrt(fro);
-    int s = 0;
-    while (fro > 0.5) { fro *= 0.5; ++s; }
-    const double sc = ldexp(1.0, -s);
-    double2 X[BSE_MAX_BANDS * BSE_MAX_BANDS], term[BSE_MAX_BANDS * BSE_MAX_BANDS], tmp[BSE_MAX_BANDS * BSE_MAX_BANDS];
-    for (int i = 0; i < n * n; ++i) {
-        X[i] = make_double2(-A[i].y * sc, A[i].x * sc);
-        E[i] = make_double2((i / n == i % n) ? 1.0 : 0.0, 0.0);
-        term[i] = E[i];
-    }
-    for (int k = 1; k <= 24; ++k) {
-        dmat_mul(term, X, tmp, n);
-        for (int i = 0; i < n * n; ++i) {
-            term[i] = cscale(tmp[i], 1.0 / k);
-            E[i] = cadd(E[i], term[i]);
-        }
-    }
-    for (int q = 0; q < s; ++q) {
-        dmat_mul(E, E, tmp, n);
-        for (int i = 0; i < n * n; ++i) E[i] = tmp[i];
-    }
 }
 
 // One CTA per sampled dense pair (k, k'): the t x t blocks of the explicit

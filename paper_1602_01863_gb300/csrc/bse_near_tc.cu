@@ -41,8 +41,8 @@
 //                  copy, every thread 16-byte cp.async gathers of X rows, and
 //                  cp.async.mbarrier.arrive signals the stage when they land
 //   (warps 2-3 only join the epilogue)
-// Pipeline: a 4-stage ring for stage 1; D1 single (TMEM), B double and Ahat
-// triple buffered (shared memory), so the converters and the head loader of
+// Pipeline: a 6-stage ring for stage 1; D1 single (TMEM), B and Ahat double
+// buffered (shared memory), so the converters and the head loader of
 // slot i work while the tensor cores run stage 2 of slot i - 1 and stage 1 of
 // slot i + 1.
 // Constraints: 2 <= t <= 16, N_div <= 64, FP32 vectors, <= 3 chains per launch.
@@ -62,8 +62,8 @@ namespace {
 
 constexpr int NT_THREADS = 384;
 constexpr int NT_KB = 32;                    // source rows per stage-1 K-block
-constexpr int NT_STAGES = 4;                 // stage-1 ring depth
-constexpr int NT_NA = 3;                     // head-operand buffers
+constexpr int NT_STAGES = 6;                 // stage-1 ring depth
+constexpr int NT_NA = 2;                     // head-operand buffers
 constexpr int S_BYTES = 128 * NT_KB * 2;     // one S image K-block: 8 KB (FP16, K-major, 64 B rows)
 constexpr int XB_BYTES = NT_KB * 64;         // X tile per chain: 32 rows x 64 B (MN-major, 64-byte swizzle)
 constexpr int A_BYTES = 256 * 128;           // Ahat: 256 rows x 64 FP16 (128 B) = 32 KB
@@ -80,14 +80,6 @@ __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvt
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
 }
-__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(su32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(su32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_arrive_noinc(uint32_t bar) {
     asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
@@ -192,7 +184,7 @@ struct NtLayout {
     __host__ __device__ NtLayout(int nch) {
         N1 = 32 * nch;
         N2 = 64 * nch;
-        b_off = NT_NA * A_BYTES;                          // Ahat: [3 buffers][256 rows][128 B]
+        b_off = NT_NA * A_BYTES;                          // Ahat: [NT_NA buffers][256 rows][128 B]
         ring_off = b_off + 2 * N2 * 128;                  // B: [2 buffers][N2 rows][128 B]
         stage_bytes = S_BYTES + nch * XB_BYTES;           // ring stage: S K-block | X tile per chain
         tab_off = ring_off + NT_STAGES * stage_bytes;     // slot tables
@@ -606,7 +598,8 @@ float bse_near_tc_xscale(const bse_interp* s, double norm) {
     return pow2_floor(32768.0 / b);
 }
 
-int bse_near_tc_launch(bse_ctx* ctx, const bse_interp* s, int nchains, const void* Xh, const float* xscale, void* U) {
+int bse_near_tc_launch(bse_ctx* ctx, const bse_interp* s, int nchains, const void* Xh, const float* xscale, void* U,
+                       bool prio, int prio_value) {
     // at most three chains per launch (TMEM: 160 columns per chain)
     for (int c0 = 0; c0 < nchains; c0 += 3) {
         const int nch = std::min(3, nchains - c0);
@@ -618,11 +611,23 @@ int bse_near_tc_launch(bse_ctx* ctx, const bse_interp* s, int nchains, const voi
             BSE_CUDA_TRY(ctx, cudaFuncSetAttribute(k_near_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         const size_t xoff = (size_t)c0 * s->nk * 8 * s->nf_tc_tpad;
         const size_t uoff = (size_t)c0 * s->nk * 8 * s->t;
-        k_near_tc<<<s->co->nkc, NT_THREADS, smem, ctx->stream>>>(
-            (const __half2*)Xh + xoff, s->nf_tc_tpad, s->d_tc_slots, (const unsigned short*)s->d_tc_rows,
-            (const unsigned char*)s->d_tc_kinfo, s->nf_tc_nsl, s->nf_tc_nkg, s->d_tc_simg, s->d_tc_aimg, s->n, s->nd, s->nv, s->nc, s->nb1, s->smin,
-            s->ns1, s->rmin, s->nr1, nch,
-            xscale + c0, s->nf_tc_sb, (float)s->co->alpha, (float2*)U + uoff, ctx->d_status);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(s->co->nkc);
+        cfg.blockDim = dim3(NT_THREADS);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = ctx->stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributePriority;
+        attr[0].val.priority = prio_value;
+        cfg.attrs = prio ? attr : nullptr;
+        cfg.numAttrs = prio ? 1 : 0;
+        BSE_CUDA_TRY(ctx, cudaLaunchKernelEx(&cfg, k_near_tc, (const __half2*)Xh + xoff, s->nf_tc_tpad,
+                                             (const int4*)s->d_tc_slots, (const unsigned short*)s->d_tc_rows,
+                                             (const unsigned char*)s->d_tc_kinfo, s->nf_tc_nsl, s->nf_tc_nkg,
+                                             (const unsigned char*)s->d_tc_simg, (const unsigned char*)s->d_tc_aimg, s->n,
+                                             s->nd, s->nv, s->nc, s->nb1, s->smin, s->ns1, s->rmin, s->nr1, nch,
+                                             xscale + c0, s->nf_tc_sb, (float)s->co->alpha, (float2*)U + uoff,
+                                             ctx->d_status));
     }
     return BSE_OK;
 }

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <type_traits>
 
+#include "bse_dmat.cuh"
 #include "bse_internal.cuh"
 
 namespace {
@@ -19,43 +20,9 @@ struct Mat {
     double2 v[BSE_MAX_BANDS * BSE_MAX_BANDS];
 };
 
-__device__ void mat_mul(const Mat& A, const Mat& B, Mat& C, int n) {
-    for (int i = 0; i < n; ++i)
-        for (int j = 0; j < n; ++j) {
-            double2 s = make_double2(0.0, 0.0);
-            for (int k = 0; k < n; ++k) s = cadd(s, cmul(A.v[i * n + k], B.v[k * n + j]));
-            C.v[i * n + j] = s;
-        }
-}
 
-// E = expm(i A) for Hermitian A by scaling and squaring of the Taylor series:
-// X = i A / 2^s with ||A||_F / 2^s <= 1/2, E = sum_{k<=24} X^k / k!, then s squarings.
-__device__ void expm_i(const Mat& A, int n, Mat& E) {
-    double fro = 0.0;
-    for (int i = 0; i < n * n; ++i) fro += A.v[i].x * A.v[i].x + A.v[i].y * A.v[i].y;
-    fro = sqrt(fro);
-    int s = 0;
-    while (fro > 0.5) { fro *= 0.5; ++s; }
-    const double sc = ldexp(1.0, -s);
-    Mat X, term, tmp;
-    for (int i = 0; i < n * n; ++i) X.v[i] = make_double2(-A.v[i].y * sc, A.v[i].x * sc);   // i A / 2^s
-    for (int i = 0; i < n * n; ++i) {
-        E.v[i] = make_double2((i / n == i % n) ? 1.0 : 0.0, 0.0);
-        term.v[i] = E.v[i];
-    }
-    for (int k = 1; k <= 24; ++k) {
-        mat_mul(term, X, tmp, n);
-        const double inv = 1.0 / k;
-        for (int i = 0; i < n * n; ++i) {
-            term.v[i] = cscale(tmp.v[i], inv);
-            E.v[i] = cadd(E.v[i], term.v[i]);
-        }
-    }
-    for (int q = 0; q < s; ++q) {
-        mat_mul(E, E, tmp, n);
-        for (int i = 0; i < n * n; ++i) E.v[i] = tmp.v[i];
-    }
-}
+// E = expm(i A) for Hermitian A (dmat_expm_i: scaling and squaring of the Taylor series).
+__device__ void expm_i(const Mat& A, int n, Mat& E) { dmat_expm_i(A.v, n, E.v); }
 
 // Fractional coordinate of point p of an (n * nd)^3 grid in coarse-major order.
 __device__ inline void point_frac(int p, int n, int nd, double k[3], int g[3]) {

@@ -8,12 +8,16 @@
 // hi and lo halves summed, so the Q operand carries ~16 mantissa bits while
 // K_c carries BF16's 8.
 //
-// Schedule: the Nc/128 row tiles x ldk/64 k-blocks form one sequence of
-// k-blocks; CTA g of G (one per SM) streams the contiguous range
-// [g T / G, (g + 1) T / G), so every SM moves the same number of K_c bytes.
-// A CTA's range touches at most a few row tiles; each touched tile yields one
-// partial accumulator ("segment") written to scratch, and k_tc_reduce sums the
-// segments of each tile in CTA order (deterministic).
+// Schedule: each row tile's k-blocks are cut into chunks of a few k-blocks;
+// the CTAs (at most one per SM) take chunks from a global counter, so a CTA
+// that starts late (the apply can run beside the near field and pick up SMs
+// as that kernel's last wave leaves them) simply takes fewer.  Each chunk's
+// two accumulators (double-buffered in TMEM) go to its own slot of a partial
+// buffer; the epilogue warp that completes the last quarter-chunk of a row
+// tile sums that tile's chunks in chunk order (deterministic, whichever CTAs
+// computed them) and writes R.  The last CTA to finish resets the counters.
+// Pipeline depth and chunk length are picked per K_c shape by timing
+// (`tune`).
 //
 // Warp roles (192 threads): warp 0 TMA producer, warp 1 MMA issuer and TMEM
 // owner, warps 2-5 epilogue (TMEM lanes 32 (w % 4) .. + 31).  Every mbarrier
@@ -35,7 +39,6 @@ namespace {
 constexpr int BM = 128;          // rows per tile (MMA M)
 constexpr int BK = 64;           // BF16 elements per k-block (128 bytes: one swizzle row)
 constexpr int BN = 16;           // MMA N: split-BF16 Q columns
-constexpr int STAGES = 5;
 constexpr int A_TILE_BYTES = BM * BK * 2;                  // 16 KB
 constexpr int B_TILE_BYTES = BN * BK * 2;                  // 2 KB
 constexpr int STAGE_BYTES = 2 * A_TILE_BYTES + B_TILE_BYTES;
@@ -131,23 +134,34 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Scheduling constants of one tensor-core K_c apply: the row tiles' k-blocks
+// are cut into chunks of chunk_kb k-blocks (the last chunk of a row may be
+// shorter); CTAs take chunks from a global counter in order.
+struct TcSched {
+    int kb_row;       // k-blocks per row tile (ldk / BK)
+    int chunk_kb;     // k-blocks per chunk
+    int chunks_row;   // chunks per row tile
+    int total;        // chunks of all row tiles
+    int Nc, nchains;
+};
+
+// Counters (ints, zero between launches): [0] next chunk, [1] CTAs finished,
+// [2 + tile] epilogue warps done with a chunk of that row tile.
+template <int STAGES>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_apply(const __grid_constant__ CUtensorMap map_kr,
                                                            const __grid_constant__ CUtensorMap map_ki,
-                                                           const __grid_constant__ CUtensorMap map_b, int kblocks_per_row,
-                                                           long long total_blocks, int seg_max,
-                                                           float* __restrict__ part, int* __restrict__ status,
+                                                           const __grid_constant__ CUtensorMap map_b, const TcSched sc,
+                                                           float* __restrict__ part, int* __restrict__ ctr,
+                                                           float2* __restrict__ R, int* __restrict__ status,
                                                            long long wait_cycles) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    __shared__ uint64_t bar_full[STAGES], bar_empty[STAGES], bar_acc_full[2], bar_acc_empty[2], bar_drain;
+    __shared__ uint64_t bar_full[STAGES], bar_empty[STAGES], bar_acc_full[2], bar_acc_empty[2], bar_cid[2], bar_drain;
+    __shared__ int stage_meta[STAGES];   // chunk * 4 + first k-block (1) + last k-block (2); -1: no further chunk
+    __shared__ int acc_meta[2];          // chunk held by an accumulator buffer; -1: no further chunk
     __shared__ uint32_t tmem_base_sh;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int G = gridDim.x, g = blockIdx.x;
-    const long long q0 = (long long)g * total_blocks / G, q1 = (long long)(g + 1) * total_blocks / G;
-    const int KB = kblocks_per_row;
-    const int nseg = (q1 > q0) ? (int)((q1 - 1) / KB - q0 / KB + 1) : 0;
-
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(smem_u32(&bar_full[s]), 1);
@@ -156,6 +170,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_apply(const __grid_constan
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&bar_acc_full[b]), 1);
             mbar_init(smem_u32(&bar_acc_empty[b]), 128);
+            mbar_init(smem_u32(&bar_cid[b]), 1);
         }
         mbar_init(smem_u32(&bar_drain), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -175,40 +190,52 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_apply(const __grid_constan
             // ---------------------------------------------------- TMA producer
             long long it = 0;
             bool ok = true;
-            for (long long q = q0; q < q1 && ok; ++q, ++it) {
-                const int s = (int)(it % STAGES);
-                if (it >= STAGES) ok = mbar_wait(smem_u32(&bar_empty[s]), (uint32_t)(((it / STAGES) - 1) & 1), status, wait_cycles);
-                if (!ok) break;
-                const int tile = (int)(q / KB), kb = (int)(q % KB);
-                unsigned char* st = smem + (size_t)s * STAGE_BYTES;
-                const uint32_t fb = smem_u32(&bar_full[s]);
-                mbar_arrive_expect_tx(fb, STAGE_BYTES);
-                tma_load_2d(smem_u32(st), &map_kr, fb, kb * BK, tile * BM);
-                tma_load_2d(smem_u32(st + A_TILE_BYTES), &map_ki, fb, kb * BK, tile * BM);
-                tma_load_2d(smem_u32(st + 2 * A_TILE_BYTES), &map_b, fb, kb * BK, 0);
+            int c = atomicAdd(&ctr[0], 1);
+            while (ok && c < sc.total) {
+                const int cn = atomicAdd(&ctr[0], 1);            // the next chunk, taken while this one streams
+                const int tile = c / sc.chunks_row, j = c - tile * sc.chunks_row;
+                const int kb0 = j * sc.chunk_kb, kb1 = min(kb0 + sc.chunk_kb, sc.kb_row);
+                for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                    const int s = (int)(it % STAGES);
+                    if (it >= STAGES &&
+                        !(ok = mbar_wait(smem_u32(&bar_empty[s]), (uint32_t)(((it / STAGES) - 1) & 1), status, wait_cycles)))
+                        break;
+                    stage_meta[s] = c * 4 + (kb == kb0 ? 1 : 0) + (kb + 1 == kb1 ? 2 : 0);
+                    unsigned char* st = smem + (size_t)s * STAGE_BYTES;
+                    const uint32_t fb = smem_u32(&bar_full[s]);
+                    mbar_arrive_expect_tx(fb, STAGE_BYTES);
+                    tma_load_2d(smem_u32(st), &map_kr, fb, kb * BK, tile * BM);
+                    tma_load_2d(smem_u32(st + A_TILE_BYTES), &map_ki, fb, kb * BK, tile * BM);
+                    tma_load_2d(smem_u32(st + 2 * A_TILE_BYTES), &map_b, fb, kb * BK, 0);
+                }
+                c = cn;
             }
-            // drain: the last (up to STAGES) issued stages must have landed before exit
-            const long long issued = it;
-            for (long long j = (issued > STAGES ? issued - STAGES : 0); j < issued; ++j)
-                mbar_wait(smem_u32(&bar_full[j % STAGES]), (uint32_t)((j / STAGES) & 1), status);
+            if (ok) {                                            // end marker for the issuer
+                const int s = (int)(it % STAGES);
+                if (it < STAGES || mbar_wait(smem_u32(&bar_empty[s]), (uint32_t)(((it / STAGES) - 1) & 1), status, wait_cycles)) {
+                    stage_meta[s] = -1;
+                    mbar_arrive(smem_u32(&bar_full[s]));
+                    ++it;
+                }
+            }
+            // drain: the copies of the last (up to STAGES) stages land before exit
+            for (long long q = (it > STAGES ? it - STAGES : 0); q < it; ++q)
+                mbar_wait(smem_u32(&bar_full[q % STAGES]), (uint32_t)((q / STAGES) & 1), status);
         }
     } else if (warp == 1) {
         if (lane == 0) {
             // ----------------------------------------------------- MMA issuer
-            long long it = 0;
             int seg = 0;
-            bool ok = true;
-            for (long long q = q0; q < q1 && ok; ++q, ++it) {
-                const bool first = (q == q0) || (q % KB == 0);
-                const bool last = (q + 1 == q1) || ((q + 1) % KB == 0);
-                const int ab = seg & 1;
-                if (first && seg >= 2) {
-                    ok = mbar_wait(smem_u32(&bar_acc_empty[ab]), (uint32_t)(((seg >> 1) - 1) & 1), status, wait_cycles);
-                    if (!ok) break;
-                }
+            for (long long it = 0;; ++it) {
                 const int s = (int)(it % STAGES);
-                ok = mbar_wait(smem_u32(&bar_full[s]), (uint32_t)((it / STAGES) & 1), status, wait_cycles);
-                if (!ok) break;
+                if (!mbar_wait(smem_u32(&bar_full[s]), (uint32_t)((it / STAGES) & 1), status, wait_cycles)) break;
+                const int meta = *reinterpret_cast<volatile int*>(&stage_meta[s]);
+                if (meta < 0) break;
+                const bool first = (meta & 1) != 0, last = (meta & 2) != 0;
+                const int ab = seg & 1;
+                if (first && seg >= 2 &&
+                    !mbar_wait(smem_u32(&bar_acc_empty[ab]), (uint32_t)(((seg >> 1) - 1) & 1), status, wait_cycles))
+                    break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t st = smem_u32(smem + (size_t)s * STAGE_BYTES);
                 const uint64_t dr = smem_desc(st), di = smem_desc(st + A_TILE_BYTES), db = smem_desc(st + 2 * A_TILE_BYTES);
@@ -221,64 +248,96 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_apply(const __grid_constan
                 }
                 mma_commit(smem_u32(&bar_empty[s]));
                 if (last) {
+                    acc_meta[ab] = meta >> 2;
                     mma_commit(smem_u32(&bar_acc_full[ab]));
+                    mbar_arrive(smem_u32(&bar_cid[ab]));        // publishes acc_meta to the epilogue
                     ++seg;
                 }
+            }
+            // no further chunk (also after a wait gave up): tell the epilogue
+            const int ab = seg & 1;
+            if (seg < 2 || mbar_wait(smem_u32(&bar_acc_empty[ab]), (uint32_t)(((seg >> 1) - 1) & 1), status, wait_cycles)) {
+                acc_meta[ab] = -1;
+                mbar_arrive(smem_u32(&bar_cid[ab]));
             }
             mma_commit(smem_u32(&bar_drain));
             mbar_wait(smem_u32(&bar_drain), 0, status);
         }
     } else {
         // ---------------------------------------------------------- epilogue
+        // Each chunk's accumulators go to part[chunk] (128 rows x 32 FP32).  The
+        // warp that finishes the last quarter-chunk of a row tile sums that
+        // tile's chunks in chunk order (deterministic, whichever CTAs computed
+        // them) and writes R = (D_r[Re] - D_i[Im], D_r[Im] + D_i[Re]) with the
+        // hi and lo halves summed.
         const int quarter = warp & 3;
         const int row = quarter * 32 + lane;
-        for (int j = 0; j < nseg; ++j) {
+        for (int j = 0;; ++j) {
             const int ab = j & 1;
-            const bool ok = mbar_wait(smem_u32(&bar_acc_full[ab]), (uint32_t)((j >> 1) & 1), status, wait_cycles);
+            bool ok = mbar_wait(smem_u32(&bar_cid[ab]), (uint32_t)((j >> 1) & 1), status, wait_cycles);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            const int chunk = *reinterpret_cast<volatile int*>(&acc_meta[ab]);
+            if (chunk < 0) break;
+            ok = mbar_wait(smem_u32(&bar_acc_full[ab]), (uint32_t)((j >> 1) & 1), status, wait_cycles);
             if (!__all_sync(0xffffffffu, ok)) break;       // warp-uniform: tcgen05.ld is warp-collective
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             float v[32];
             tmem_ld32(tmem_base + ((uint32_t)(quarter * 32) << 16) + ab * ACC_COLS, v);
-            float4* dst = reinterpret_cast<float4*>(part + (((size_t)g * seg_max + j) * BM + row) * 32);
+            float4* dst = reinterpret_cast<float4*>(part + ((size_t)chunk * BM + row) * 32);
 #pragma unroll
             for (int i = 0; i < 8; ++i) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             mbar_arrive(smem_u32(&bar_acc_empty[ab]));
+            __threadfence();
+            __syncwarp();
+            const int tile = chunk / sc.chunks_row;
+            int done = 0;
+            if (lane == 0) done = atomicAdd(&ctr[2 + tile], 1) == 4 * sc.chunks_row - 1;
+            done = __shfl_sync(0xffffffffu, done, 0);
+            if (!done) continue;
+            __threadfence();
+            for (int q = 0; q < 4; ++q) {
+                const int r = q * 32 + lane, i = tile * BM + r;
+                float acc[32];
+#pragma unroll
+                for (int k = 0; k < 32; ++k) acc[k] = 0.f;
+                for (int cc = tile * sc.chunks_row; cc < (tile + 1) * sc.chunks_row; ++cc) {
+                    const float4* src = reinterpret_cast<const float4*>(part + ((size_t)cc * BM + r) * 32);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const float4 w = __ldcg(src + k);
+                        acc[4 * k] += w.x; acc[4 * k + 1] += w.y; acc[4 * k + 2] += w.z; acc[4 * k + 3] += w.w;
+                    }
+                }
+                if (i < sc.Nc) {
+                    const float* Dr = acc;          // columns 0..15: Kr B^T
+                    const float* Di = acc + 16;     // columns 16..31: Ki B^T
+                    const int p = sc.nchains;
+                    for (int ch = 0; ch < p; ++ch) {
+                        const float re = (Dr[ch] + Dr[2 * p + ch]) - (Di[p + ch] + Di[3 * p + ch]);
+                        const float im = (Dr[p + ch] + Dr[3 * p + ch]) + (Di[ch] + Di[2 * p + ch]);
+                        R[(size_t)ch * sc.Nc + i] = make_float2(re, im);
+                    }
+                }
+            }
+            if (lane == 0) ctr[2 + tile] = 0;               // ready for the next launch
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS));
-}
-
-// Sum the segments of each row tile (CTA order) and combine the split
-// accumulators into complex R [chain][Nc] (FP32).
-__global__ void k_tc_reduce(const float* __restrict__ part, const int* __restrict__ tile_cta, const long long* __restrict__ cta_q0,
-                            int kblocks_per_row, int seg_max, int Nc, int nchains, float2* __restrict__ R) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= Nc) return;
-    const int tile = i / BM, r = i % BM;
-    const int g_lo = tile_cta[2 * tile], g_hi = tile_cta[2 * tile + 1];
-    float acc[32];
-#pragma unroll
-    for (int c = 0; c < 32; ++c) acc[c] = 0.f;
-    for (int g = g_lo; g <= g_hi; ++g) {
-        const int j = tile - (int)(cta_q0[g] / kblocks_per_row);
-        const float4* src = reinterpret_cast<const float4*>(part + (((size_t)g * seg_max + j) * BM + r) * 32);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const float4 v = src[q];
-            acc[4 * q] += v.x; acc[4 * q + 1] += v.y; acc[4 * q + 2] += v.z; acc[4 * q + 3] += v.w;
+    if (threadIdx.x == 0) {
+        // the last CTA of the launch resets the counters (every tile counter too
+        // when a wait gave up and some tiles never completed)
+        __threadfence();
+        if (atomicAdd(&ctr[1], 1) == (int)gridDim.x - 1) {
+            if (*reinterpret_cast<volatile int*>(status) & 1)
+                for (int t2 = 0; t2 < sc.total / sc.chunks_row; ++t2) ctr[2 + t2] = 0;
+            ctr[0] = 0;
+            ctr[1] = 0;
+            __threadfence();
         }
-    }
-    const float* Dr = acc;          // columns 0..15: Kr B^T
-    const float* Di = acc + 16;     // columns 16..31: Ki B^T
-    const int p = nchains;
-    for (int c = 0; c < p; ++c) {
-        const float re = (Dr[c] + Dr[2 * p + c]) - (Di[p + c] + Di[3 * p + c]);
-        const float im = (Dr[p + c] + Dr[3 * p + c]) + (Di[c] + Di[2 * p + c]);
-        R[(size_t)c * Nc + i] = make_float2(re, im);
     }
 }
 
@@ -322,122 +381,150 @@ int make_map(bse_ctx* ctx, CUtensorMap* m, const void* base, int ldk, int rows, 
     return BSE_OK;
 }
 
+// Launch shape of the tensor-core apply: pipeline depth, chunk length and CTA
+// count, and where the counters sit behind the chunk partials.
 struct TcPlan {
-    int kblocks_per_row = 0, tiles = 0, ctas = 0, seg_max = 0;
-    long long total = 0;
-    std::vector<long long> q0;      // [ctas + 1]
-    std::vector<int> tile_cta;      // [2 * tiles]
+    int stages = 5, ctas = 0;
+    TcSched sc{};
+    size_t part_bytes = 0;   // chunk partials: total x 128 x 32 FP32
+    size_t ctr_off = 0;      // byte offset of the counters (2 + row tiles ints)
+    size_t bytes = 0;        // partials + counters
 };
 
-TcPlan plan_for(int Nc, int ldk, int sm_count) {
+size_t tc_smem(int stages) { return (size_t)stages * STAGE_BYTES + 1024; }
+
+TcPlan plan_for(int Nc, int ldk, int stages, int chunk_kb, int sm_count) {
     TcPlan p;
-    p.kblocks_per_row = ldk / BK;
-    p.tiles = (Nc + BM - 1) / BM;
-    p.total = (long long)p.tiles * p.kblocks_per_row;
-    p.ctas = (int)std::min<long long>(std::max(sm_count, 1), p.total);
-    p.q0.resize(p.ctas + 1);
-    for (int g = 0; g <= p.ctas; ++g) p.q0[g] = (long long)g * p.total / p.ctas;
-    p.seg_max = 0;
-    for (int g = 0; g < p.ctas; ++g) {
-        const long long a = p.q0[g], b = p.q0[g + 1];
-        const int nseg = (b > a) ? (int)((b - 1) / p.kblocks_per_row - a / p.kblocks_per_row + 1) : 0;
-        p.seg_max = std::max(p.seg_max, nseg);
-    }
-    p.tile_cta.resize(2 * p.tiles);
-    for (int t = 0; t < p.tiles; ++t) {
-        const long long lo = (long long)t * p.kblocks_per_row, hi = lo + p.kblocks_per_row - 1;
-        int glo = -1, ghi = -1;
-        for (int g = 0; g < p.ctas; ++g) {
-            if (p.q0[g + 1] > lo && p.q0[g] <= hi) {
-                if (glo < 0) glo = g;
-                ghi = g;
-            }
-        }
-        p.tile_cta[2 * t] = glo;
-        p.tile_cta[2 * t + 1] = ghi;
-    }
+    p.stages = stages;
+    p.sc.kb_row = ldk / BK;
+    p.sc.chunk_kb = std::max(1, std::min(chunk_kb, p.sc.kb_row));
+    p.sc.chunks_row = (p.sc.kb_row + p.sc.chunk_kb - 1) / p.sc.chunk_kb;
+    const int tiles = (Nc + BM - 1) / BM;
+    p.sc.total = tiles * p.sc.chunks_row;
+    p.sc.Nc = Nc;
+    p.sc.nchains = 1;
+    p.ctas = std::max(1, std::min(std::max(sm_count, 1), p.sc.total));
+    p.part_bytes = sizeof(float) * (size_t)p.sc.total * BM * 32;
+    p.ctr_off = (p.part_bytes + 255) / 256 * 256;
+    p.bytes = p.ctr_off + sizeof(int) * (size_t)(2 + tiles);
     return p;
 }
 
 struct TcState {
     CUtensorMap map_kr, map_ki, map_b;
     TcPlan plan;
-    int* d_tile_cta = nullptr;
-    long long* d_q0 = nullptr;
 };
+
+bool g_attr_set[7] = {};
+
+int set_smem_attr(bse_ctx* ctx, int stages) {
+    if (g_attr_set[stages]) return BSE_OK;
+    cudaError_t e = cudaSuccess;
+    switch (stages) {
+        case 4: e = cudaFuncSetAttribute(k_tc_apply<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem(4)); break;
+        case 5: e = cudaFuncSetAttribute(k_tc_apply<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem(5)); break;
+        case 6: e = cudaFuncSetAttribute(k_tc_apply<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem(6)); break;
+        default: ctx->err = "unsupported tensor-core pipeline depth"; return BSE_ERR_ARG;
+    }
+    if (e != cudaSuccess) {
+        ctx->err = std::string("k_tc_apply shared memory attribute: ") + cudaGetErrorString(e);
+        return BSE_ERR_CUDA;
+    }
+    g_attr_set[stages] = true;
+    return BSE_OK;
+}
+
+// One launch; `prio` != 0 sets the launch's scheduling priority to `prio_value`
+// (the apply then yields SMs to higher-priority kernels that run beside it).
+cudaError_t launch_tc(const TcState& st, const TcPlan& p, const CUtensorMap& map_b, void* part_ctr, float2* R,
+                      int nchains, int* status, long long wait, cudaStream_t stream, bool prio, int prio_value) {
+    TcSched sc = p.sc;
+    sc.nchains = nchains;
+    float* part = static_cast<float*>(part_ctr);
+    int* ctr = reinterpret_cast<int*>(static_cast<unsigned char*>(part_ctr) + p.ctr_off);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(p.ctas);
+    cfg.blockDim = dim3(TC_THREADS);
+    cfg.dynamicSmemBytes = tc_smem(p.stages);
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributePriority;
+    attr[0].val.priority = prio_value;
+    cfg.attrs = prio ? attr : nullptr;
+    cfg.numAttrs = prio ? 1 : 0;
+    switch (p.stages) {
+        case 4: return cudaLaunchKernelEx(&cfg, k_tc_apply<4>, st.map_kr, st.map_ki, map_b, sc, part, ctr, R, status, wait);
+        case 5: return cudaLaunchKernelEx(&cfg, k_tc_apply<5>, st.map_kr, st.map_ki, map_b, sc, part, ctr, R, status, wait);
+        default: return cudaLaunchKernelEx(&cfg, k_tc_apply<6>, st.map_kr, st.map_ki, map_b, sc, part, ctr, R, status, wait);
+    }
+}
 
 }  // namespace
 
 namespace {
 
+struct TcChoice { int stages, chunk_kb; };
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int>, int> g_tuned_ctas;     // (N_c, ldk, SM count) -> CTA count
+std::map<std::tuple<int, int, int>, TcChoice> g_tuned;     // (N_c, ldk, SM count) -> launch shape
 
-// Autotuner for the persistent split of the k-block sequence: times the
-// tensor-core apply (+ reduce) for a few CTA counts on the handle's own K_c
-// with CUDA events and keeps the fastest; the choice is cached per shape.
-int tune_ctas(bse_ctx* ctx, bse_interp* s, const CUtensorMap& mkr, const CUtensorMap& mki, const CUtensorMap& mb) {
+// Autotuner of the tensor-core apply's launch shape: times every (pipeline
+// depth, chunk length) candidate on the handle's own K_c with CUDA events
+// (3 warm-up + 10 timed launches each) and keeps the fastest; the choice is
+// cached per (N_c, ldk, SM count) for the process.
+TcChoice tune(bse_ctx* ctx, bse_interp* s, TcState& st) {
     const bse_coarse* c = s->co;
     const auto key = std::make_tuple(c->Nc, c->ldk, ctx->sm_count);
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
-        auto it = g_tuned_ctas.find(key);
-        if (it != g_tuned_ctas.end()) return it->second;
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) return it->second;
     }
-    const int sm = std::max(ctx->sm_count, 1);
-    const long long total = (long long)((c->Nc + BM - 1) / BM) * (c->ldk / BK);
-    std::vector<int> cand;
-    for (int d : {1, 2, 4, 8}) {
-        const int g = (int)std::min<long long>(std::max(sm / d, 1), total);
-        if (std::find(cand.begin(), cand.end(), g) == cand.end()) cand.push_back(g);
-    }
-    const int g34 = (int)std::min<long long>(std::max(3 * sm / 4, 1), total);
-    if (std::find(cand.begin(), cand.end(), g34) == cand.end()) cand.push_back(g34);
-    size_t part_bytes = 0;
-    for (int g : cand) {
-        const TcPlan p = plan_for(c->Nc, c->ldk, g);
-        part_bytes = std::max(part_bytes, sizeof(float) * (size_t)p.ctas * p.seg_max * BM * 32);
-    }
-    float* d_part = nullptr;
-    if (bse_alloc(ctx, (void**)&d_part, part_bytes, "autotune partials") != BSE_OK) return sm;
+    const int kb_row = c->ldk / BK;
+    std::vector<TcChoice> cand;
+    for (int stages : {4, 5, 6})
+        for (int ck : {8, 16, 32, 64}) {
+            const int ckc = std::min(ck, kb_row);
+            bool dup = false;
+            for (const TcChoice& x : cand) dup = dup || (x.stages == stages && x.chunk_kb == ckc);
+            if (!dup) cand.push_back({stages, ckc});
+        }
+    size_t bytes = 0;
+    for (const TcChoice& x : cand) bytes = std::max(bytes, plan_for(c->Nc, c->ldk, x.stages, x.chunk_kb, ctx->sm_count).bytes);
+    TcChoice best = {5, std::min(16, kb_row)};
+    void* d_buf = nullptr;
+    if (bse_alloc(ctx, &d_buf, bytes, "autotune partials") != BSE_OK) { cudaGetLastError(); return best; }
+    cudaMemset(d_buf, 0, bytes);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    int best = cand[0];
     float best_ms = 1e30f;
-    for (int g : cand) {
-        const TcPlan p = plan_for(c->Nc, c->ldk, g);
-        int* d_tc = nullptr;
-        long long* d_q = nullptr;
-        if (bse_alloc(ctx, (void**)&d_tc, sizeof(int) * p.tile_cta.size(), "autotune tables") != BSE_OK) continue;
-        if (bse_alloc(ctx, (void**)&d_q, sizeof(long long) * p.q0.size(), "autotune tables") != BSE_OK) { cudaFree(d_tc); continue; }
-        cudaMemcpy(d_tc, p.tile_cta.data(), sizeof(int) * p.tile_cta.size(), cudaMemcpyHostToDevice);
-        cudaMemcpy(d_q, p.q0.data(), sizeof(long long) * p.q0.size(), cudaMemcpyHostToDevice);
-        auto launch = [&]() {
-            k_tc_apply<<<p.ctas, TC_THREADS, STAGES * STAGE_BYTES + 1024, ctx->stream>>>(
-                mkr, mki, mb, p.kblocks_per_row, p.total, p.seg_max, d_part, ctx->d_status, WAIT_CYCLES);
-            k_tc_reduce<<<(c->Nc + 127) / 128, 128, 0, ctx->stream>>>(d_part, d_tc, d_q, p.kblocks_per_row, p.seg_max,
-                                                                     c->Nc, 1, (float2*)s->d_R);
-        };
-        for (int r = 0; r < 3; ++r) launch();
+    for (const TcChoice& x : cand) {
+        if (set_smem_attr(ctx, x.stages) != BSE_OK) continue;
+        const TcPlan p = plan_for(c->Nc, c->ldk, x.stages, x.chunk_kb, ctx->sm_count);
+        // the counters sit behind this candidate's partials: start them at zero
+        cudaMemsetAsync(static_cast<unsigned char*>(d_buf) + p.ctr_off, 0, p.bytes - p.ctr_off, ctx->stream);
+        bool ok = true;
+        for (int r = 0; r < 3 && ok; ++r)
+            ok = launch_tc(st, p, st.map_b, d_buf, (float2*)s->d_R, 1, ctx->d_status, WAIT_CYCLES, ctx->stream, false, 0) == cudaSuccess;
         cudaEventRecord(e0, ctx->stream);
         const int reps = 10;
-        for (int r = 0; r < reps; ++r) launch();
+        for (int r = 0; r < reps && ok; ++r)
+            ok = launch_tc(st, p, st.map_b, d_buf, (float2*)s->d_R, 1, ctx->d_status, WAIT_CYCLES, ctx->stream, false, 0) == cudaSuccess;
         cudaEventRecord(e1, ctx->stream);
         float ms = 0.f;
-        if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms / reps < best_ms) {
+        if (ok && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
+            ms / reps < best_ms) {
             best_ms = ms / reps;
-            best = g;
+            best = x;
         }
-        cudaFree(d_tc);
-        cudaFree(d_q);
     }
+    cudaStreamSynchronize(ctx->stream);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFree(d_part);
+    cudaFree(d_buf);
     cudaGetLastError();
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tuned_ctas[key] = best;
+    g_tuned[key] = best;
     return best;
 }
 
@@ -449,11 +536,6 @@ int bse_tc_prepare(bse_ctx* ctx, bse_interp* s) {
     if ((rc = bse_alloc(ctx, (void**)&s->d_Bop, sizeof(__nv_bfloat16) * BN * (size_t)c->ldk, "split-BF16 operand")) != BSE_OK)
         return rc;
     BSE_CUDA_TRY(ctx, cudaMemset(s->d_Bop, 0, sizeof(__nv_bfloat16) * BN * (size_t)c->ldk));
-    static bool attr_set = false;
-    if (!attr_set) {
-        BSE_CUDA_TRY(ctx, cudaFuncSetAttribute(k_tc_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, STAGES * STAGE_BYTES + 1024));
-        attr_set = true;
-    }
     TcState* st = new TcState();
     if ((rc = make_map(ctx, &st->map_kr, c->d_kr, c->ldk, c->Nc, BM)) != BSE_OK ||
         (rc = make_map(ctx, &st->map_ki, c->d_ki, c->ldk, c->Nc, BM)) != BSE_OK ||
@@ -461,54 +543,44 @@ int bse_tc_prepare(bse_ctx* ctx, bse_interp* s) {
         delete st;
         return rc;
     }
-    const int ctas = tune_ctas(ctx, s, st->map_kr, st->map_ki, st->map_b);
-    st->plan = plan_for(c->Nc, c->ldk, ctas);
+    const TcChoice ch = tune(ctx, s, *st);
+    if ((rc = set_smem_attr(ctx, ch.stages)) != BSE_OK) { delete st; return rc; }
+    st->plan = plan_for(c->Nc, c->ldk, ch.stages, ch.chunk_kb, ctx->sm_count);
     const TcPlan& p = st->plan;
-    if ((rc = bse_alloc(ctx, (void**)&s->d_part, sizeof(float) * (size_t)p.ctas * p.seg_max * BM * 32, "tile partials")) != BSE_OK ||
-        (rc = bse_alloc(ctx, (void**)&st->d_tile_cta, sizeof(int) * p.tile_cta.size(), "tile schedule")) != BSE_OK ||
-        (rc = bse_alloc(ctx, (void**)&st->d_q0, sizeof(long long) * p.q0.size(), "cta schedule")) != BSE_OK) {
-        cudaFree(st->d_tile_cta); cudaFree(st->d_q0);
+    if ((rc = bse_alloc(ctx, (void**)&s->d_part, p.bytes, "chunk partials")) != BSE_OK) {
         delete st;
         return rc;
     }
-    BSE_CUDA_TRY(ctx, cudaMemcpy(st->d_tile_cta, p.tile_cta.data(), sizeof(int) * p.tile_cta.size(), cudaMemcpyHostToDevice));
-    BSE_CUDA_TRY(ctx, cudaMemcpy(st->d_q0, p.q0.data(), sizeof(long long) * p.q0.size(), cudaMemcpyHostToDevice));
+    BSE_CUDA_TRY(ctx, cudaMemset(s->d_part, 0, p.bytes));
     s->tc_ctas = p.ctas;
-    s->tc_kblocks = p.kblocks_per_row;
+    s->tc_kblocks = p.sc.chunk_kb;
+    s->tc_stages = p.stages;
     s->tc_state = st;
     return BSE_OK;
 }
 
 void bse_tc_release(bse_interp* s) {
     if (!s || !s->tc_state) return;
-    TcState* st = reinterpret_cast<TcState*>(s->tc_state);
-    cudaFree(st->d_tile_cta);
-    cudaFree(st->d_q0);
-    delete st;
+    delete reinterpret_cast<TcState*>(s->tc_state);
     s->tc_state = nullptr;
 }
 
-int bse_tc_apply(bse_ctx* ctx, bse_interp* s, int nchains) {
-    const bse_coarse* c = s->co;
+int bse_tc_apply(bse_ctx* ctx, bse_interp* s, int nchains, cudaStream_t stream, bool prio, int prio_value) {
     const TcState* st = reinterpret_cast<const TcState*>(s->tc_state);
-    const TcPlan& p = st->plan;
-    k_tc_apply<<<p.ctas, TC_THREADS, STAGES * STAGE_BYTES + 1024, ctx->stream>>>(
-        st->map_kr, st->map_ki, st->map_b, p.kblocks_per_row, p.total, p.seg_max, s->d_part, ctx->d_status,
-        ctx->wait_cycles > 0 ? ctx->wait_cycles : WAIT_CYCLES);
-    k_tc_reduce<<<(c->Nc + 127) / 128, 128, 0, ctx->stream>>>(s->d_part, st->d_tile_cta, st->d_q0, p.kblocks_per_row,
-                                                             p.seg_max, c->Nc, nchains, (float2*)s->d_R);
+    BSE_CUDA_TRY(ctx, launch_tc(*st, st->plan, st->map_b, s->d_part, (float2*)s->d_R, nchains, ctx->d_status,
+                                ctx->wait_cycles > 0 ? ctx->wait_cycles : WAIT_CYCLES, stream, prio, prio_value));
     return BSE_OK;
 }
 
-// Bytes of the tile partials one tensor-core K_c apply writes.
+// Bytes of the chunk partials and counters one tensor-core K_c apply uses.
 size_t bse_tc_part_bytes(const bse_interp* s) {
-    const TcState* st = reinterpret_cast<const TcState*>(s->tc_state);
-    return sizeof(float) * (size_t)st->plan.ctas * st->plan.seg_max * BM * 32;
+    return reinterpret_cast<const TcState*>(s->tc_state)->plan.bytes;
 }
 
 // Tensor-core K_c apply with a caller-supplied operand buffer `bop` [16][ldk]
-// (zeroed by the caller where unused), tile partials `part` and output R: a
-// tensor map for `bop` is encoded on the stack; nothing is allocated.
+// (zeroed by the caller where unused), partials + counters `part`
+// (bse_tc_part_bytes) and output R: the counters are cleared on the stream and
+// a tensor map for `bop` is encoded on the stack; nothing is allocated.
 int bse_tc_apply_scratch(bse_ctx* ctx, const bse_interp* s, int nchains, __nv_bfloat16* bop, float* part, void* R) {
     const bse_coarse* c = s->co;
     const TcState* st = reinterpret_cast<const TcState*>(s->tc_state);
@@ -516,10 +588,8 @@ int bse_tc_apply_scratch(bse_ctx* ctx, const bse_interp* s, int nchains, __nv_bf
     CUtensorMap map_b;
     int rc = make_map(ctx, &map_b, bop, c->ldk, BN, BN);
     if (rc != BSE_OK) return rc;
-    k_tc_apply<<<p.ctas, TC_THREADS, STAGES * STAGE_BYTES + 1024, ctx->stream>>>(
-        st->map_kr, st->map_ki, map_b, p.kblocks_per_row, p.total, p.seg_max, part, ctx->d_status,
-        ctx->wait_cycles > 0 ? ctx->wait_cycles : WAIT_CYCLES);
-    k_tc_reduce<<<(c->Nc + 127) / 128, 128, 0, ctx->stream>>>(part, st->d_tile_cta, st->d_q0, p.kblocks_per_row,
-                                                             p.seg_max, c->Nc, nchains, (float2*)R);
+    BSE_CUDA_TRY(ctx, cudaMemsetAsync(reinterpret_cast<unsigned char*>(part) + p.ctr_off, 0, p.bytes - p.ctr_off, ctx->stream));
+    BSE_CUDA_TRY(ctx, launch_tc(*st, p, map_b, part, (float2*)R, nchains, ctx->d_status,
+                                ctx->wait_cycles > 0 ? ctx->wait_cycles : WAIT_CYCLES, ctx->stream, false, 0));
     return BSE_OK;
 }
