@@ -33,8 +33,9 @@ sys.path.insert(0, ROOT)
 
 N_OMEGA = 1000
 # DRAM bytes (read + write) of one near-field launch on this workload from the
-# committed ncu capture, or None when the kernel changed since the capture.
-NEAR_TRAFFIC = None
+# committed ncu capture (profiles/k_near_tc_single_system.md: 425.3 + 55.1 MB),
+# or None when the kernel changed since the capture.
+NEAR_TRAFFIC = 480.4e6
 
 
 def parse():

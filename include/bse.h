@@ -173,8 +173,9 @@ typedef struct bse_dense_inputs {
  * |delta|^2 <= floor(width_w^2 n_div^2 + 1e-9).
  * `vec_prec` (F64 or F32) is the precision of the Lanczos vectors and of the
  * restrict / prolong / near-field arithmetic; the Lanczos reductions sum
- * across threads and blocks in FP64 in every mode (with F32 vectors each
- * thread first sums its few products, at most 2 t, in FP32).  The coarse
+ * across warps and blocks in FP64 in every mode (with F32 vectors each
+ * thread first sums its few products in FP32, and the ||w||^2 of the Lanczos
+ * update is also summed over a warp's 32 threads in FP32).  The coarse
  * handle must outlive the interp handle.
  * With BF16 K_c the set-up autotunes the tensor-core apply: it times a few
  * splits of the K_c stream over the SMs on this K_c and keeps the fastest

@@ -12,6 +12,7 @@
 // orthonormal axes), |q|, onehot(vc) [t], onehot(v'c') [t], dE_vc(k),
 // dE_v'c'(k').  Target: N_k (K_explicit - K_M1) (Re, Im).
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "bse_dmat.cuh"
@@ -507,16 +508,75 @@ __global__ void k_to_grid(const typename Cx<T>::V* __restrict__ psi, int nchains
     grid[(((size_t)ch * t + tr) * L + x) * L * L + (size_t)y * L + z] = make_float2((float)v.x, (float)v.y);
 }
 
-// per frequency: out[ch][e1][xi] = sum_e2 That[e1][e2][xi] in[ch][e2][xi]
-__global__ void k_freq_mul(const float2* __restrict__ That, const float2* __restrict__ in, int nchains, int t, int L3,
-                           float2* __restrict__ out) {
+// per frequency: out[ch][e1][xi] = sum_e2 That[e1][e2][xi] in[ch][e2][xi]; one
+// thread per (e1, xi) serves every chain, so That is read once.
+__global__ void __launch_bounds__(256) k_freq_mul(const float2* __restrict__ That, const float2* __restrict__ in,
+                                                  int nchains, int t, int L3, float2* __restrict__ out) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)nchains * t * L3) return;
-    const int ch = (int)(i / ((long long)t * L3)), e1 = (int)((i / L3) % t), xi = (int)(i % L3);
-    float2 acc = make_float2(0.f, 0.f);
-    for (int e2 = 0; e2 < t; ++e2)
-        acc = cadd(acc, cmul(That[((size_t)e1 * t + e2) * L3 + xi], in[((size_t)ch * t + e2) * L3 + xi]));
-    out[i] = acc;
+    if (i >= (long long)t * L3) return;
+    const int e1 = (int)(i / L3), xi = (int)(i % L3);
+    float2 acc[BSE_MAX_CHAINS];
+#pragma unroll
+    for (int ch = 0; ch < BSE_MAX_CHAINS; ++ch) acc[ch] = make_float2(0.f, 0.f);
+    for (int e2 = 0; e2 < t; ++e2) {
+        const float2 T = That[((size_t)e1 * t + e2) * L3 + xi];
+#pragma unroll
+        for (int ch = 0; ch < BSE_MAX_CHAINS; ++ch)
+            if (ch < nchains) acc[ch] = cadd(acc[ch], cmul(T, in[((size_t)ch * t + e2) * L3 + xi]));
+    }
+#pragma unroll
+    for (int ch = 0; ch < BSE_MAX_CHAINS; ++ch)
+        if (ch < nchains) out[((size_t)ch * t + e1) * L3 + xi] = acc[ch];
+}
+
+// One axis of the separable DFT, in place, on [chan][L][L][L] (L <= 64): a CTA
+// stages 32 lines along `axis` in shared memory (loads and stores coalesced),
+// and warp w computes the outputs k = w, w + 8, ... of line `lane`:
+// out_k = sum_n in_n w^{k n} with w^j = tw[j] (n ascending, the table index
+// advanced as in k_dft_axis, so the two give the same sums).
+__global__ void __launch_bounds__(256) k_dft_tile(float2* __restrict__ a, int L, long long nlines, int axis,
+                                                  const float2* __restrict__ tw_g) {
+    extern __shared__ float2 dsm[];
+    const int P = (L & 1) ? L + 2 : L + 1;              // odd row pitch: conflict-free 8-byte rows
+    float2* tw = dsm;
+    float2* din = tw + 64;
+    float2* dout = din + 32 * P;
+    const long long L2 = (long long)L * L, L3 = L2 * L;
+    const long long g0 = (long long)blockIdx.x * 32;
+    for (int j = threadIdx.x; j < L; j += blockDim.x) tw[j] = tw_g[j];
+    // line g = (ch L + u) L + v; element n of it at base + n * stride
+    auto base = [&](long long g) -> long long {
+        const long long ch = g / L2;
+        const int u = (int)((g / L) % L), v = (int)(g % L);
+        if (axis == 0) return ch * L3 + (long long)u * L + v;
+        if (axis == 1) return ch * L3 + (long long)u * L2 + v;
+        return ch * L3 + (long long)u * L2 + (long long)v * L;
+    };
+    const long long stride = axis == 0 ? L2 : (axis == 1 ? L : 1);
+    const int n_el = 32 * L;
+    for (int i = threadIdx.x; i < n_el; i += blockDim.x) {
+        const int l = axis == 2 ? i / L : i % 32, n = axis == 2 ? i % L : i / 32;
+        const long long g = g0 + l;
+        if (g < nlines) din[l * P + n] = a[base(g) + n * stride];
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int k = warp; k < L; k += 8) {
+        float2 acc = make_float2(0.f, 0.f);
+        int ph = 0;
+        for (int n = 0; n < L; ++n) {
+            acc = cadd(acc, cmul(din[lane * P + n], tw[ph]));
+            ph += k;
+            if (ph >= L) ph -= L;
+        }
+        dout[lane * P + k] = acc;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n_el; i += blockDim.x) {
+        const int l = axis == 2 ? i / L : i % 32, n = axis == 2 ? i % L : i / 32;
+        const long long g = g0 + l;
+        if (g < nlines) a[base(g) + n * stride] = dout[l * P + n];
+    }
 }
 
 // w[ch][kd t + tr] += grid[ch][tr][g(kd)] / L^3, and block partials of <psi, w>
@@ -529,21 +589,41 @@ __global__ void __launch_bounds__(BSE_VEC_THREADS) k_add_learned(const float2* _
     const int nk = n * n * n * nd * nd * nd, Ndiv = nd * nd * nd, L = n * nd;
     const long long N = (long long)nk * t;
     double2 dot[BSE_MAX_CHAINS];
-    for (int c = 0; c < BSE_MAX_CHAINS; ++c) dot[c] = make_double2(0.0, 0.0);
+    float2 dotf[BSE_MAX_CHAINS];
+    for (int c = 0; c < BSE_MAX_CHAINS; ++c) {
+        dot[c] = make_double2(0.0, 0.0);
+        dotf[c] = make_float2(0.f, 0.f);
+    }
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
         const int kd = (int)(i / t), tr = (int)(i % t);
         const Int3 ci = unflat3(kd / Ndiv, n), j = unflat3(kd % Ndiv, nd);
         const int x = ci.a * nd + j.a, y = ci.b * nd + j.b, z = ci.c * nd + j.c;
         for (int ch = 0; ch < nchains; ++ch) {
             const float2 gv = grid[(((size_t)ch * t + tr) * L + x) * L * L + (size_t)y * L + z];
-            const double2 wv = to_d2(w[(size_t)ch * N + i]);
-            const V nw = from_d2<V>(make_double2(wv.x + (double)gv.x * scale, wv.y + (double)gv.y * scale));
-            w[(size_t)ch * N + i] = nw;
-            const double2 p = to_d2(psi[(size_t)ch * N + i]), q = to_d2(nw);
-            for (int c = 0; c < BSE_MAX_CHAINS; ++c)
-                if (c == ch) { dot[c].x += p.x * q.x + p.y * q.y; dot[c].y += p.x * q.y - p.y * q.x; }
+            if constexpr (std::is_same<T, float>::value) {
+                // FP32 vectors: the update and this thread's products in FP32 (FP64 is slow per
+                // element on GB300); the sums over threads below stay FP64
+                const float2 wv = w[(size_t)ch * N + i];
+                const float2 nw = make_float2(fmaf(gv.x, scale, wv.x), fmaf(gv.y, scale, wv.y));
+                w[(size_t)ch * N + i] = nw;
+                const float2 p = psi[(size_t)ch * N + i];
+                for (int c = 0; c < BSE_MAX_CHAINS; ++c)
+                    if (c == ch) {
+                        dotf[c].x = fmaf(p.x, nw.x, fmaf(p.y, nw.y, dotf[c].x));
+                        dotf[c].y = fmaf(p.x, nw.y, fmaf(-p.y, nw.x, dotf[c].y));
+                    }
+            } else {
+                const double2 wv = to_d2(w[(size_t)ch * N + i]);
+                const V nw = from_d2<V>(make_double2(wv.x + (double)gv.x * scale, wv.y + (double)gv.y * scale));
+                w[(size_t)ch * N + i] = nw;
+                const double2 p = to_d2(psi[(size_t)ch * N + i]), q = to_d2(nw);
+                for (int c = 0; c < BSE_MAX_CHAINS; ++c)
+                    if (c == ch) { dot[c].x += p.x * q.x + p.y * q.y; dot[c].y += p.x * q.y - p.y * q.x; }
+            }
         }
     }
+    if constexpr (std::is_same<T, float>::value)
+        for (int c = 0; c < BSE_MAX_CHAINS; ++c) dot[c] = make_double2((double)dotf[c].x, (double)dotf[c].y);
     for (int c = 0; c < BSE_MAX_CHAINS; ++c) red[c][threadIdx.x] = dot[c];
     __syncthreads();
     for (int st = BSE_VEC_THREADS / 2; st > 0; st >>= 1) {
@@ -556,6 +636,20 @@ __global__ void __launch_bounds__(BSE_VEC_THREADS) k_add_learned(const float2* _
 
 int dft3(bse_ctx* ctx, float2* a, float2* tmp, int L, long long nchan, const float2* tw) {
     const long long tot = nchan * L * L * L;
+    if (L <= 64) {
+        // in place, one tile of 32 lines per CTA and axis
+        const long long nlines = nchan * L * L;
+        const int P = (L & 1) ? L + 2 : L + 1;
+        const size_t smem = sizeof(float2) * (64 + 2 * 32 * (size_t)P);
+        static bool attr = false;
+        if (!attr) {
+            BSE_CUDA_TRY(ctx, cudaFuncSetAttribute(k_dft_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
+            attr = true;
+        }
+        const unsigned blocks = (unsigned)((nlines + 31) / 32);
+        for (int axis = 0; axis < 3; ++axis) k_dft_tile<<<blocks, 256, smem, ctx->stream>>>(a, L, nlines, axis, tw);
+        return BSE_OK;
+    }
     const int blocks = (int)((tot + 255) / 256);
     k_dft_axis<<<blocks, 256, 0, ctx->stream>>>(a, tmp, L, nchan, 0, tw);
     k_dft_axis<<<blocks, 256, 0, ctx->stream>>>(tmp, a, L, nchan, 1, tw);
@@ -581,7 +675,7 @@ int bse_apply_learned(bse_ctx* ctx, const bse_interp* s, int nchains, const void
         k_to_grid<float><<<(int)((tot + 255) / 256), 256, 0, ctx->stream>>>((const float2*)psi, nchains, s->n, s->nd, t, g);
     int rc = dft3(ctx, g, tmp, L, nchan, s->d_tw_fwd);
     if (rc != BSE_OK) return rc;
-    k_freq_mul<<<(int)((nchan * L3 + 255) / 256), 256, 0, ctx->stream>>>(s->d_lker, g, nchains, t, (int)L3, tmp);
+    k_freq_mul<<<(int)(((long long)t * L3 + 255) / 256), 256, 0, ctx->stream>>>(s->d_lker, g, nchains, t, (int)L3, tmp);
     rc = dft3(ctx, tmp, g, L, nchan, s->d_tw_inv);
     if (rc != BSE_OK) return rc;
     const int nb = (int)std::min<long long>(std::max<long long>((s->N + BSE_VEC_THREADS - 1) / BSE_VEC_THREADS, 1), BSE_MAX_VEC_BLOCKS);
