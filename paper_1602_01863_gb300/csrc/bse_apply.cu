@@ -2330,8 +2330,11 @@ int launch_near_rb(bse_ctx* ctx, const bse_interp* s, int nchains, const void* X
     const int smem = (int)bytes;
     if (smem > 48 * 1024)
         BSE_CUDA_TRY(ctx, cudaFuncSetAttribute(k_near_cell_rb<NV, NC, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    // one thread per active (target, corner) pair; with at most 256 pairs and no
+    // register prefetch, 256-thread CTAs let two CTAs share an SM (128 registers)
     dim3 grid(s->co->nkc, nchains);
-    k_near_cell_rb<NV, NC, PF><<<grid, 512, smem, ctx->stream>>>(
+    const int bd = (PF == 0 && s->npairs <= 256) ? 256 : 512;
+    k_near_cell_rb<NV, NC, PF><<<grid, bd, smem, ctx->stream>>>(
         (const float2*)X, s->d_clist, s->d_cstart, s->d_pairs, s->npairs, (const float*)s->d_hd, s->n_near,
         (const float2*)s->d_Hv, (const float2*)s->d_Hc, (const float*)s->d_hc, s->n, s->nd, s->smin, s->ns1, s->rmin,
         s->nr1, (float2*)U);

@@ -531,9 +531,8 @@ __global__ void __launch_bounds__(256) k_freq_mul(const float2* __restrict__ Tha
 
 // One axis of the separable DFT, in place, on [chan][L][L][L] (L <= 64): a CTA
 // stages 32 lines along `axis` in shared memory (loads and stores coalesced),
-// and warp w computes the outputs k = w, w + 8, ... of line `lane`:
-// out_k = sum_n in_n w^{k n} with w^j = tw[j] (n ascending, the table index
-// advanced as in k_dft_axis, so the two give the same sums).
+// and warp w computes outputs w, w + 8, ... of line `lane`:
+// out_k = sum_n in_n w^{k n} with w^j = tw[j], in two stages (below).
 __global__ void __launch_bounds__(256) k_dft_tile(float2* __restrict__ a, int L, long long nlines, int axis,
                                                   const float2* __restrict__ tw_g) {
     extern __shared__ float2 dsm[];
@@ -561,21 +560,45 @@ __global__ void __launch_bounds__(256) k_dft_tile(float2* __restrict__ a, int L,
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int k = warp; k < L; k += 8) {
+    // Two-stage Cooley-Tukey with L = A B (A the largest divisor <= sqrt L):
+    // n = B n1 + n2, k = k1 + A k2,
+    //   Y[n2][k1] = w^{n2 k1} sum_{n1} x[B n1 + n2] w^{B n1 k1}      (stage 1, into dout)
+    //   X[k1 + A k2] = sum_{n2} Y[n2][k1] w^{A n2 k2}                 (stage 2, into din)
+    // with every power of w read from the table (index mod L).
+    int A = 1;
+    for (int d = 2; d * d <= L; ++d)
+        if (L % d == 0) A = d;
+    const int B = L / A;
+    for (int q = warp; q < L; q += 8) {
+        const int n2 = q / A, k1 = q - n2 * A;
         float2 acc = make_float2(0.f, 0.f);
         int ph = 0;
-        for (int n = 0; n < L; ++n) {
-            acc = cadd(acc, cmul(din[lane * P + n], tw[ph]));
-            ph += k;
+        const int dph = (B * k1) % L;
+        for (int n1 = 0; n1 < A; ++n1) {
+            acc = cadd(acc, cmul(din[lane * P + B * n1 + n2], tw[ph]));
+            ph += dph;
             if (ph >= L) ph -= L;
         }
-        dout[lane * P + k] = acc;
+        dout[lane * P + q] = cmul(acc, tw[(n2 * k1) % L]);
+    }
+    __syncthreads();
+    for (int k = warp; k < L; k += 8) {
+        const int k2 = k / A, k1 = k - k2 * A;
+        float2 acc = make_float2(0.f, 0.f);
+        int ph = 0;
+        const int dph = (A * k2) % L;
+        for (int n2 = 0; n2 < B; ++n2) {
+            acc = cadd(acc, cmul(dout[lane * P + n2 * A + k1], tw[ph]));
+            ph += dph;
+            if (ph >= L) ph -= L;
+        }
+        din[lane * P + k] = acc;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < n_el; i += blockDim.x) {
         const int l = axis == 2 ? i / L : i % 32, n = axis == 2 ? i % L : i / 32;
         const long long g = g0 + l;
-        if (g < nlines) a[base(g) + n * stride] = dout[l * P + n];
+        if (g < nlines) a[base(g) + n * stride] = din[l * P + n];
     }
 }
 
