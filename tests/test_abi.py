@@ -88,6 +88,7 @@ def test_null_arguments_are_rejected_on_the_host(built_lib):
         "bse_set_stop_rule": lambda: lib.bse_set_stop_rule(N, ctypes.c_double(0.01), 10, ctypes.c_double(1.0),
                                                            ctypes.c_double(0.1), 4, dummy),
         "bse_interp_info": lambda: lib.bse_interp_info(N, lldummy),
+        "bse_interp_kc_plan": lambda: lib.bse_interp_kc_plan(N, idummy),
         "bse_ctx_set_wait_limit": lambda: lib.bse_ctx_set_wait_limit(N, ctypes.c_longlong(0)),
         "bse_dipoles": lambda: lib.bse_dipoles(N, N, 1, dummy, N, dummy),
         "bse_apply_h": lambda: lib.bse_apply_h(N, N, 1, N, N),

@@ -1,5 +1,6 @@
 """Parity of the default mixed path: BF16 / complex64 K_c, FP32 vectors and the
-tensor-core (TF32) Method-3 near field, i.e. what the benchmark times.
+tensor-core Method-3 near field (FP16 operands with power-of-two scales: 10
+explicit mantissa bits, as TF32), i.e. what the benchmark times.
 
 Bars
   * Spectrum (Sec. 5.1 accuracy measure, peak-normalised Im eps): 1e-3 against
@@ -133,3 +134,24 @@ def test_single_system_default_path_spectrum(ctx):
     print("a_1..a_10 max relative difference:", float(np.max(np.abs(a_m[:, :10] - a_p[:, :10]) / np.abs(a_p[:, :10]))))
     assert max(errs) <= 1e-3
     assert np.all(np.abs(a_m[:, :10] - a_p[:, :10]) <= 1e-3 * np.abs(a_p[:, :10]))
+
+
+def test_concurrent_kc_apply_matches_serial_schedule(ctx):
+    """With the tensor-core near field the K_c apply runs beside it (auxiliary
+    stream, lowest scheduling priority) and its CTAs take chunks of K_c from a
+    counter; the tile sums run in chunk order, so the Haydock coefficients of
+    the graph run, the eager run and the profiled run (kernels one after
+    another) are equal bit for bit.  The autotuned launch shape is reported."""
+    from paper_1602_01863_gb300 import bse
+    m = synth.draw_model(31, 4, 4)
+    co, it = _system(ctx, m, 6, 4, bse.SCHEME_M3, bse.PREC_BF16)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    stages, chunk, ctas = it.kc_plan()
+    assert stages in (4, 5, 6) and 1 <= chunk <= 64 and 1 <= ctas <= sms
+    dirs = np.eye(3)
+    runs = [ctx.bse_haydock_run([it], [3], dirs, 40, f) for f in (bse.USE_GRAPH, 0, bse.PROFILE, bse.USE_GRAPH)]
+    for a, b, pn2, sd, _ in runs[1:]:
+        assert np.array_equal(a, runs[0][0]) and np.array_equal(b, runs[0][1])
+    assert np.all(np.isfinite(runs[0][0])) and np.all(runs[0][1][:, 1:] > 0)
+    it.free()
+    co.free()
