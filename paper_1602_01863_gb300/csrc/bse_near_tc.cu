@@ -33,7 +33,11 @@
 // |x| <= ||d_v||_F ||d_c||_F ||psi||_2, and |y1 s_x s_b|, |z s_x s_b| <= 2^15 from
 // |y1| <= h_max sqrt(n_near) ||x||_2; c / 1 and h_head c are at most h_max.
 //
-// Warp roles (384 threads, one CTA per coarse cell):
+// Grid: one CTA per coarse cell, except that the cells of a last wave that
+// would leave at least half of the SMs idle get two CTAs each, over the two
+// halves of the slot list; their results add (two FP32 additions onto zero,
+// order-independent) into U, which the host zeroes for those cells.
+// Warp roles (384 threads):
 //   warp 0         MMA issuer (lane 0) and TMEM owner
 //   warp 1         head loader (lane 0): eight 4 KB bulk copies per slot
 //   warps 4-7      converters (TMEM lane quarter = warp % 4)
@@ -196,7 +200,7 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_near_tc(
     const unsigned short* __restrict__ krows, const unsigned char* __restrict__ kslot, int nsl, int nkg,
     const unsigned char* __restrict__ Simg, const unsigned char* __restrict__ Aimg, int n, int nd, int nv, int nc,
     int nb1, int smin, int ns1, int rmin, int nr1, int nch, const float* __restrict__ xscale, float sb, float alpha,
-    float2* __restrict__ U, int* __restrict__ status) {
+    float2* __restrict__ U, int* __restrict__ status, int nwhole) {
     // an earlier launch on this context gave up a wait: skip (the host reports BSE_ERR_TIMEOUT)
     if (*reinterpret_cast<volatile int*>(status) & 2) return;
     extern __shared__ unsigned char raw[];
@@ -212,7 +216,18 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_near_tc(
     constexpr int nmh = 2;
     const NtLayout lay(nch);
     const int N1 = lay.N1, N2 = lay.N2;
-    const int cell = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // Blocks below nwhole take a whole cell; the others take half of the slots
+    // of a cell (two blocks per cell: the cells of a last, partly filled wave),
+    // and their halves add into U, which the host zeroed for those cells.
+    int cell = blockIdx.x, s_lo = 0, s_hi = nsl;
+    const bool split = (int)blockIdx.x >= nwhole;
+    if (split) {
+        const int u = blockIdx.x - nwhole, mid = nsl / 2;
+        cell = nwhole + (u >> 1);
+        s_lo = (u & 1) ? mid : 0;
+        s_hi = (u & 1) ? nsl : mid;
+    }
     unsigned char* A2 = sm;
     unsigned char* B2 = sm + lay.b_off;
     unsigned char* ring = sm + lay.ring_off;
@@ -261,6 +276,8 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_near_tc(
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_sh, tD1 = tmem + (uint32_t)(nmh * N2);
+    const int4* s_slv = s_sl + s_lo;                       // this block's slots
+    const int nslv = s_hi - s_lo;
 
     if (warp == W_ISS) {
         // ------------------------------------------------------------ MMA issuer
@@ -269,12 +286,12 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_near_tc(
             const uint32_t a0 = su32(A2), b0 = su32(B2), r0 = su32(ring);
             bool ok = true;
             int kg = 0;
-            for (int i = 0; i <= nsl && ok; ++i) {
-                if (i < nsl) {
+            for (int i = 0; i <= nslv && ok; ++i) {
+                if (i < nslv) {
                     // stage 1 of slot i into D1 (the converters have read D1 of slot i - 1)
                     if (i > 0) ok = bar_wait(su32(&bar_d1_free), (uint32_t)((i - 1) & 1), status, abort_flag);
                     tc_fence_after();
-                    const int nkb = s_sl[i].z;
+                    const int nkb = s_slv[i].z;
                     for (int kb = 0; kb < nkb && ok; ++kb, ++kg) {
                         const int q = kg % NT_STAGES;
                         ok = bar_wait(su32(&bar_full[q]), (uint32_t)((kg / NT_STAGES) & 1), status, abort_flag);
@@ -317,7 +334,7 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_near_tc(
         // becomes row (chain, j) of B, columns Y or Z (16-byte chunks 0-3 or 4-7).
         const int quarter = warp & 3, L = quarter * 32 + lane, yz = L >> 6, j = L & 63;
         bool ok = true;
-        for (int i = 0; i < nsl; ++i) {
+        for (int i = 0; i < nslv; ++i) {
             ok = ok && bar_wait(su32(&bar_d1_full), (uint32_t)(i & 1), status, abort_flag);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) break;
@@ -362,10 +379,11 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_near_tc(
         const uint32_t doff = (uint32_t)((r >> 3) * 512 + (r & 7) * 64 + (((c ^ (r >> 1)) & 3) << 4));
         bool ok = true;
         int issued = 0;
-        for (int kg = 0; kg < nkg; ++kg) {
-            const int q = kg % NT_STAGES;
-            if (kg >= NT_STAGES) {
-                if (lane == 0) ok = bar_wait(su32(&bar_empty[q]), (uint32_t)(((kg / NT_STAGES) - 1) & 1), status, abort_flag);
+        const int kg0 = s_slv[0].y, kg1 = s_slv[nslv - 1].y + s_slv[nslv - 1].z;   // this block's K-blocks
+        for (int kg = kg0; kg < kg1; ++kg) {
+            const int kl = kg - kg0, q = kl % NT_STAGES;
+            if (kl >= NT_STAGES) {
+                if (lane == 0) ok = bar_wait(su32(&bar_empty[q]), (uint32_t)(((kl / NT_STAGES) - 1) & 1), status, abort_flag);
                 ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             }
             if (!ok) break;
@@ -397,11 +415,11 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_near_tc(
         if (lane == 0) {
             bool ok = true;
             int issued = 0;
-            for (int i = 0; i < nsl && ok; ++i) {
+            for (int i = 0; i < nslv && ok; ++i) {
                 const int bsel = i % NT_NA;
                 if (i >= NT_NA) ok = bar_wait(su32(&bar_a_free[bsel]), (uint32_t)(((i / NT_NA) - 1) & 1), status, abort_flag);
                 if (!ok) break;
-                const Int3 so = unflat3(s_sl[i].x, ns1);
+                const Int3 so = unflat3(s_slv[i].x, ns1);
                 const int oa = so.a + smin - rmin, ob = so.b + smin - rmin, oc = so.c + smin - rmin;
                 const uint32_t ab = su32(A2 + bsel * A_BYTES), bar = su32(&bar_a_full[bsel]);
                 bar_arrive_tx(bar, 8 * AH_BYTES);
@@ -440,8 +458,16 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_near_tc(
             for (int jj = 0; jj < 32; ++jj) {
                 const float other = __shfl_xor_sync(0xffffffffu, v[jj], 1);
                 const int jt = j0 + jj;
-                if (ri == 0 && e < t && jt < Ndiv && interp_active(jt, l, nd, nb1))
-                    U[(((size_t)ch * nk + (size_t)cell * Ndiv + jt) * 8 + l) * t + e] = make_float2(v[jj] * f, other * f);
+                if (ri == 0 && e < t && jt < Ndiv && interp_active(jt, l, nd, nb1)) {
+                    float2* u = U + (((size_t)ch * nk + (size_t)cell * Ndiv + jt) * 8 + l) * t + e;
+                    if (split) {
+                        // exactly two additions onto zero: the sum does not depend on their order
+                        atomicAdd(&u->x, v[jj] * f);
+                        atomicAdd(&u->y, other * f);
+                    } else {
+                        *u = make_float2(v[jj] * f, other * f);
+                    }
+                }
             }
         }
     }
@@ -611,8 +637,18 @@ int bse_near_tc_launch(bse_ctx* ctx, const bse_interp* s, int nchains, const voi
             BSE_CUDA_TRY(ctx, cudaFuncSetAttribute(k_near_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         const size_t xoff = (size_t)c0 * s->nk * 8 * s->nf_tc_tpad;
         const size_t uoff = (size_t)c0 * s->nk * 8 * s->t;
+        // One CTA per coarse cell fills the SMs in waves; when the last wave
+        // would leave at least half of them idle, its cells are split over two
+        // CTAs each (halves of the slots), whose results add into a zeroed U.
+        const int nkc = s->co->nkc, S = std::max(ctx->sm_count, 1), rem = nkc % S;
+        const int ntail = (s->nf_tc_nsl >= 2 && rem > 0 && 2 * rem <= S) ? rem : 0;
+        const int nwhole = nkc - ntail;
+        if (ntail > 0)
+            for (int ch = 0; ch < nch; ++ch)
+                BSE_CUDA_TRY(ctx, cudaMemsetAsync((float2*)U + uoff + ((size_t)ch * s->nk + (size_t)nwhole * s->Ndiv) * 8 * s->t, 0,
+                                                  sizeof(float2) * (size_t)ntail * s->Ndiv * 8 * s->t, ctx->stream));
         cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(s->co->nkc);
+        cfg.gridDim = dim3(nwhole + 2 * ntail);
         cfg.blockDim = dim3(NT_THREADS);
         cfg.dynamicSmemBytes = smem;
         cfg.stream = ctx->stream;
@@ -627,7 +663,7 @@ int bse_near_tc_launch(bse_ctx* ctx, const bse_interp* s, int nchains, const voi
                                              (const unsigned char*)s->d_tc_simg, (const unsigned char*)s->d_tc_aimg, s->n,
                                              s->nd, s->nv, s->nc, s->nb1, s->smin, s->ns1, s->rmin, s->nr1, nch,
                                              xscale + c0, s->nf_tc_sb, (float)s->co->alpha, (float2*)U + uoff,
-                                             ctx->d_status));
+                                             ctx->d_status, nwhole));
     }
     return BSE_OK;
 }
