@@ -42,7 +42,7 @@ void free_interp(bse_interp* s) {
                     s->d_vec[1], s->d_vec[2], s->d_part_dot, s->d_part_nrm, s->d_a, s->d_aim, s->d_b, s->d_stop,
                     s->d_basis, s->d_cgs_part, s->d_cgs_h, s->d_pairs, s->d_clist, s->d_cstart,
                     s->d_lker, s->d_lgrid, s->d_tw_fwd, s->d_tc_rows, s->d_tc_slots,
-                    s->d_tc_rowstart, s->d_tc_kinfo, s->d_tc_simg, s->d_tc_aimg, s->d_xscale, s->d_xscale_gen, s->d_H2};
+                    s->d_tc_kinfo, s->d_tc_simg, s->d_tc_aimg, s->d_xscale, s->d_xscale_gen, s->d_H2};
     for (void* p : ptrs) cudaFree(p);
     bse_tc_release(s);
     delete s;

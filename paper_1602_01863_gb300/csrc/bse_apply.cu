@@ -1182,7 +1182,7 @@ __global__ void __launch_bounds__(256) k_lanczos_axpy4(float4* __restrict__ W, c
 }
 
 // One launch for a_i, the update and b_{i+1} (FP32 vectors, no
-// reorthogonalisation; 256 threads per block, grid-stride).  GB300 issues FP64
+// reorthogonalisation; 512 threads per block, one block per SM, grid-stride).  GB300 issues FP64
 // at a small fraction of its FP32 rate, so the FP64 work here is per block or
 // per warp, never per element:
 //  * a_i: warp 0 of every block sums the <psi, w> block partials of the H
@@ -1194,13 +1194,13 @@ __global__ void __launch_bounds__(256) k_lanczos_axpy4(float4* __restrict__ W, c
 //    partials in FP64 in a fixed order into b_{i+1} and applies the breakdown
 //    test b_{i+1} < 1e-12 max_j |a_j|.
 template <int NCH>
-__global__ void __launch_bounds__(256) k_lanczos_axpy4_ab(float4* __restrict__ W, const float4* __restrict__ psi,
+__global__ void __launch_bounds__(512) k_lanczos_axpy4_ab(float4* __restrict__ W, const float4* __restrict__ psi,
                                                           const float4* __restrict__ psi_prev,
                                                           const double2* __restrict__ dot, int ndot, double* __restrict__ a,
                                                           double* __restrict__ aim, double* __restrict__ b, int step, int m,
                                                           int N4, double* __restrict__ part,
                                                           int* __restrict__ stop, int* __restrict__ ctr) {
-    __shared__ float wsum[NCH][8];
+    __shared__ float wsum[NCH][16];
     __shared__ double a_sh[NCH];
     __shared__ float ab_sh[NCH][2];
     __shared__ int run_sh[NCH];
@@ -1210,13 +1210,18 @@ __global__ void __launch_bounds__(256) k_lanczos_axpy4_ab(float4* __restrict__ W
 #pragma unroll
         for (int ch = 0; ch < NCH; ++ch) {
             const int run = stop[ch] == 0;                 // uniform over the grid until the last block
+            // the imaginary part (a Hermiticity diagnostic) in block 0 only
             double2 s = make_double2(0.0, 0.0);
-            if (run)
-                for (int i = lane; i < ndot; i += 32) s = cadd(s, dot[(size_t)ch * BSE_MAX_VEC_BLOCKS + i]);
+            if (run) {
+                if (blockIdx.x == 0)
+                    for (int i = lane; i < ndot; i += 32) s = cadd(s, dot[(size_t)ch * BSE_MAX_VEC_BLOCKS + i]);
+                else
+                    for (int i = lane; i < ndot; i += 32) s.x += dot[(size_t)ch * BSE_MAX_VEC_BLOCKS + i].x;
+            }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 s.x += __shfl_down_sync(0xffffffffu, s.x, o);
-                s.y += __shfl_down_sync(0xffffffffu, s.y, o);
+                if (blockIdx.x == 0) s.y += __shfl_down_sync(0xffffffffu, s.y, o);
             }
             if (lane == 0) {
                 run_sh[ch] = run;
@@ -1237,9 +1242,14 @@ __global__ void __launch_bounds__(256) k_lanczos_axpy4_ab(float4* __restrict__ W
         nrm[ch] = 0.f;
         if (!run_sh[ch]) continue;
         const float ai = ab_sh[ch][0], bi = ab_sh[ch][1];
-        for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < N4; g += gridDim.x * blockDim.x) {
-            const size_t o = (size_t)ch * N4 + g;
+        const int G = gridDim.x * blockDim.x;
+        // two entries per pass: both loads in flight before either update
+        for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < N4; g += 2 * G) {
+            const bool two = g + G < N4;
+            const size_t o = (size_t)ch * N4 + g, o2 = o + G;
             const float4 w = W[o], p = psi[o], q = psi_prev[o];
+            float4 w2 = make_float4(0.f, 0.f, 0.f, 0.f), p2 = w2, q2 = w2;
+            if (two) { w2 = W[o2]; p2 = psi[o2]; q2 = psi_prev[o2]; }
             float4 r;
             r.x = fmaf(-bi, q.x, fmaf(-ai, p.x, w.x));
             r.y = fmaf(-bi, q.y, fmaf(-ai, p.y, w.y));
@@ -1247,6 +1257,14 @@ __global__ void __launch_bounds__(256) k_lanczos_axpy4_ab(float4* __restrict__ W
             r.w = fmaf(-bi, q.w, fmaf(-ai, p.w, w.w));
             W[o] = r;
             nrm[ch] = fmaf(r.x, r.x, fmaf(r.y, r.y, fmaf(r.z, r.z, fmaf(r.w, r.w, nrm[ch]))));
+            if (two) {
+                r.x = fmaf(-bi, q2.x, fmaf(-ai, p2.x, w2.x));
+                r.y = fmaf(-bi, q2.y, fmaf(-ai, p2.y, w2.y));
+                r.z = fmaf(-bi, q2.z, fmaf(-ai, p2.z, w2.z));
+                r.w = fmaf(-bi, q2.w, fmaf(-ai, p2.w, w2.w));
+                W[o2] = r;
+                nrm[ch] = fmaf(r.x, r.x, fmaf(r.y, r.y, fmaf(r.z, r.z, fmaf(r.w, r.w, nrm[ch]))));
+            }
         }
     }
 #pragma unroll
@@ -1259,7 +1277,7 @@ __global__ void __launch_bounds__(256) k_lanczos_axpy4_ab(float4* __restrict__ W
     __syncthreads();
     if (threadIdx.x < NCH && run_sh[threadIdx.x]) {
         double s = 0.0;
-        for (int w = 0; w < 8; ++w) s += (double)wsum[threadIdx.x][w];
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += (double)wsum[threadIdx.x][w];
         part[(size_t)threadIdx.x * BSE_MAX_VEC_BLOCKS + blockIdx.x] = s;
     }
     __threadfence();
@@ -1890,10 +1908,11 @@ int enqueue_chains(bse_ctx* ctx, bse_interp* s, int nch, int m, bool reorth, boo
         if (vec4 && !reorth) {
             // a_i, the update and b_{i+1} in one launch, then the scale
 #define BSE_AXPY_AB(NCH_)                                                                                       \
-    k_lanczos_axpy4_ab<NCH_><<<nbab, 256, 0, st>>>((float4*)W, (const float4*)B, (const float4*)A, s->d_part_dot,    \
+    k_lanczos_axpy4_ab<NCH_><<<nbab, 512, 0, st>>>((float4*)W, (const float4*)B, (const float4*)A, s->d_part_dot,    \
                                                   dot_blocks(s), s->d_a, s->d_aim, s->d_b, i, m, N / 2, s->d_part_nrm, \
                                                   s->d_stop, s->d_lz_ctr)
-            const int nbab = std::min(nb4, 4 * std::max(ctx->sm_count, 1));
+            // one block of 512 threads per SM: every block sums the <psi, w> partials in FP64
+            const int nbab = std::min((N / 2 + 511) / 512, std::max(ctx->sm_count, 1));
             if (nch == 1) BSE_AXPY_AB(1);
             else if (nch == 2) BSE_AXPY_AB(2);
             else if (nch == 3) BSE_AXPY_AB(3);

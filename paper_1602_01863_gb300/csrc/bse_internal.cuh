@@ -190,7 +190,6 @@ struct bse_interp {
     int nf_tc_nrows = 0;             // their source rows (all slots)
     void* d_tc_rows = nullptr;       // [K-blocks][32] source rows: js | corner << 8, 0xFFFF none (ushort)
     int4* d_tc_slots = nullptr;      // per slot {slot, first K-block, K-blocks, rows}
-    int* d_tc_rowstart = nullptr;    // (unused)
     void* d_tc_kinfo = nullptr;      // [K-blocks] slot of each K-block (uchar)
     unsigned char* d_tc_simg = nullptr;   // near pattern images, 8 KB per K-block
     unsigned char* d_tc_aimg = nullptr;   // head images, 4 KB per (coarse point, relative offset)
