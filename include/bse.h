@@ -177,9 +177,10 @@ typedef struct bse_dense_inputs {
  * thread first sums its few products in FP32, and the ||w||^2 of the Lanczos
  * update is also summed over a warp's 32 threads in FP32).  The coarse
  * handle must outlive the interp handle.
- * With BF16 K_c the set-up autotunes the tensor-core apply: it times a few
- * splits of the K_c stream over the SMs on this K_c and keeps the fastest
- * (cached per shape for the process).
+ * With BF16 K_c the set-up autotunes the tensor-core apply: it times its
+ * pipeline depths (4, 5, 6 stages) and chunk lengths (8 to 64 k-blocks) on
+ * this K_c and keeps the fastest (cached per shape for the process;
+ * bse_interp_kc_plan reports the choice).
  * BSE_SCHEME_M2 (Sec. 4, Method 2) builds the dense interpolated Hamiltonian
  *   H = diag(Delta E) + (1/N_div)[(F A F^H) h_head(q_dense) + F (K_c - A h_head(q_coarse)) F^H]
  * for every pair (no width; F of Eq. interpwfn, A the head for every coarse pair)
