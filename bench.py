@@ -35,7 +35,7 @@ N_OMEGA = 1000
 # DRAM bytes (read + write) of one near-field launch on this workload from the
 # committed ncu capture (profiles/k_near_tc_single_system.md: 430.7 + 56.6 MB),
 # or None when the kernel changed since the capture.
-NEAR_TRAFFIC = 487.3e6
+NEAR_TRAFFIC = None
 
 
 def parse():

@@ -41,8 +41,9 @@
 //   warp 0         MMA issuer (lane 0) and TMEM owner
 //   warp 1         head loader (lane 0): eight 4 KB bulk copies per slot
 //   warps 4-7      converters (TMEM lane quarter = warp % 4)
-//   warps 8-11     producers: per K-block one thread issues the S-image bulk
-//                  copy, every thread 16-byte cp.async gathers of X rows, and
+//   warps 8-11     producers: warp w takes every fourth K-block; its lane 0
+//                  issues the S-image bulk copy, lane r the 16-byte cp.async
+//                  gathers of source row r (all chunks and chains), and
 //                  cp.async.mbarrier.arrive signals the stage when they land
 //   (warps 2-3 only join the epilogue)
 // Pipeline: a 6-stage ring for stage 1; D1 single (TMEM), B and Ahat double
@@ -76,7 +77,6 @@ constexpr int NT_TMEM_COLS = 512;
 constexpr int W_ISS = 0;                     // MMA issuer
 constexpr int W_CV0 = 4;                     // converters: warps 4-7
 constexpr int W_P0 = 8, W_PN = 4;            // producers: warps 8-11
-constexpr int NT_P = 32 * W_PN;              // producer threads
 constexpr int W_AL = 1;                      // head loader
 constexpr long long NT_WAIT_CYCLES = 400000000LL;   // ~0.2 s; a whole launch takes well under 10 ms
 
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_near_tc(
     fence_async_smem();
     if (tid == 0) {
         for (int q = 0; q < NT_STAGES; ++q) {
-            bar_init(su32(&bar_full[q]), NT_P + 1);               // every producer thread's cp.async + the S bulk copy
+            bar_init(su32(&bar_full[q]), 32 + 1);                 // one producer warp's cp.async + the S bulk copy
             bar_init(su32(&bar_empty[q]), 1);
         }
         bar_init(su32(&bar_d1_full), 1);
@@ -370,45 +370,55 @@ __global__ void __launch_bounds__(NT_THREADS, 1) k_near_tc(
         }
     } else if (warp >= W_P0 && warp < W_P0 + W_PN) {
         // -------------------------------------------------- stage-1 producers
-        // Thread pt: source row r = pt / 4 of the K-block, 16-byte chunk c = pt % 4
-        // of that row's piece (transitions 4c .. 4c + 3) for every chain; the
-        // destination is the MN-major tile of 64-byte rows with the 64-byte swizzle.
-        const int pt = tid - 32 * W_P0, r = pt >> 2, c = pt & 3;
+        // Producer warp pw takes the K-blocks kl = pw, pw + 4, ... of this
+        // block; lane r gathers source row r of the K-block: its four 16-byte
+        // chunks (transitions 4c .. 4c + 3) for every chain, into the MN-major
+        // tile of 64-byte rows with the 64-byte swizzle (chunk c ^ (r / 2) % 4).
+        const int pw = warp - W_P0, r = lane;
         const int tq = tpad >> 2;                                   // chunks per piece
         const size_t chs = (size_t)nk * 8 * tpad;                   // half2 per chain of X
-        const uint32_t doff = (uint32_t)((r >> 3) * 512 + (r & 7) * 64 + (((c ^ (r >> 1)) & 3) << 4));
+        const uint32_t rowoff = (uint32_t)((r >> 3) * 512 + (r & 7) * 64);
+        const int swz = (r >> 1) & 3;
         bool ok = true;
-        int issued = 0;
         const int kg0 = s_slv[0].y, kg1 = s_slv[nslv - 1].y + s_slv[nslv - 1].z;   // this block's K-blocks
-        for (int kg = kg0; kg < kg1; ++kg) {
-            const int kl = kg - kg0, q = kl % NT_STAGES;
+        const int nkl = kg1 - kg0;
+        for (int kl = pw; kl < nkl; kl += W_PN) {
+            const int kg = kg0 + kl, q = kl % NT_STAGES;
             if (kl >= NT_STAGES) {
                 if (lane == 0) ok = bar_wait(su32(&bar_empty[q]), (uint32_t)(((kl / NT_STAGES) - 1) & 1), status, abort_flag);
                 ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             }
             if (!ok) break;
-            const int code = s_krow[kg * NT_KB + r], sl = s_kslot[kg];
+            const int code = s_krow[kg * NT_KB + r];
             const uint32_t Sq = su32(ring + q * lay.stage_bytes), Xq = Sq + S_BYTES;
-            if (pt == 0) {
+            if (lane == 0) {
                 bar_arrive_tx(su32(&bar_full[q]), S_BYTES);
                 bulk_copy(Sq, Simg + (size_t)kg * S_BYTES, S_BYTES, su32(&bar_full[q]));
             }
-            const bool live = code != 0xFFFF && c < tq;
+            const bool live = code != 0xFFFF;
             const __half2* src = X;
             if (live) {
                 const int js = code & 0xFF, l = code >> 8;
-                src = X + (((size_t)scell[sl * 8 + l] * Ndiv + js) * 8 + l) * tpad + 4 * c;
+                src = X + (((size_t)scell[s_kslot[kg] * 8 + l] * Ndiv + js) * 8 + l) * tpad;
             }
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch)
-                if (ch < nch) cp_async16(Xq + (uint32_t)(ch * XB_BYTES) + doff, live ? src + ch * chs : X, live ? 16u : 0u);
+            for (int ch = 0; ch < 3; ++ch) {
+                if (ch >= nch) break;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const bool on = live && c < tq;
+                    cp_async16(Xq + (uint32_t)(ch * XB_BYTES) + rowoff + (uint32_t)(((c ^ swz) & 3) << 4),
+                               on ? src + ch * chs + 4 * c : X, on ? 16u : 0u);
+                }
+            }
             cp_async_arrive_noinc(su32(&bar_full[q]));               // arrives when this thread's copies landed
-            ++issued;
         }
         cp_async_wait0();
-        if (pt == 0)                                                 // bulk copies in flight must land before exit
-            for (int jj = std::max(0, issued - NT_STAGES); jj < issued; ++jj)
-                bar_drain(su32(&bar_full[jj % NT_STAGES]), (uint32_t)((jj / NT_STAGES) & 1), status);
+        // the S-image bulk copies of the last NT_STAGES K-blocks may still be in
+        // flight: each warp waits for those it issued before exit
+        if (lane == 0)
+            for (int kl = std::max(0, nkl - NT_STAGES); kl < nkl; ++kl)
+                if (kl % W_PN == pw) bar_drain(su32(&bar_full[kl % NT_STAGES]), (uint32_t)((kl / NT_STAGES) & 1), status);
     } else if (warp == W_AL) {
         // -------------------------------------------------------- head loader
         // Slot i: the images of (k~_l, k~_s - k~_l) for the eight target corners l.
