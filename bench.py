@@ -33,9 +33,9 @@ sys.path.insert(0, ROOT)
 
 N_OMEGA = 1000
 # DRAM bytes (read + write) of one near-field launch on this workload from the
-# committed ncu capture (profiles/k_near_tc_single_system.md: 430.7 + 56.6 MB),
+# committed ncu capture (profiles/k_near_tc_single_system.md: 428.7 + 56.5 MB),
 # or None when the kernel changed since the capture.
-NEAR_TRAFFIC = None
+NEAR_TRAFFIC = 485.2e6
 
 
 def parse():
