@@ -13,9 +13,11 @@
 // that starts late (the apply can run beside the near field and pick up SMs
 // as that kernel's last wave leaves them) simply takes fewer.  Each chunk's
 // two accumulators (double-buffered in TMEM) go to its own slot of a partial
-// buffer; the epilogue warp that completes the last quarter-chunk of a row
-// tile sums that tile's chunks in chunk order (deterministic, whichever CTAs
-// computed them) and writes R.  The last CTA to finish resets the counters.
+// buffer.  Each quarter of a row tile (32 rows) has its own counter: the
+// epilogue warp that writes the quarter's rows of the tile's last chunk sums
+// them over the tile's chunks in chunk order (deterministic, whichever CTAs
+// computed them) and writes those rows of R.  The last CTA to finish resets
+// the counters.
 // Pipeline depth and chunk length are picked per K_c shape by timing
 // (`tune`).
 //
@@ -146,7 +148,8 @@ struct TcSched {
 };
 
 // Counters (ints, zero between launches): [0] next chunk, [1] CTAs finished,
-// [2 + tile] epilogue warps done with a chunk of that row tile.
+// [2 + 4 tile + q] chunks of that row tile whose rows 32 q .. 32 q + 31 (the
+// rows of epilogue warp q) are written.
 template <int STAGES>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_apply(const __grid_constant__ CUtensorMap map_kr,
                                                            const __grid_constant__ CUtensorMap map_ki,
@@ -265,8 +268,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_apply(const __grid_constan
         }
     } else {
         // ---------------------------------------------------------- epilogue
-        // Each chunk's accumulators go to part[chunk] (128 rows x 32 FP32).  The
-        // warp that finishes the last quarter-chunk of a row tile sums that
+        // Each chunk's accumulators go to part[chunk] (128 rows x 32 FP32).  For
+        // each quarter of a row tile (the 32 rows one epilogue warp owns), the
+        // warp that writes the tile's last chunk of those rows sums them over the
         // tile's chunks in chunk order (deterministic, whichever CTAs computed
         // them) and writes R = (D_r[Re] - D_i[Im], D_r[Im] + D_i[Re]) with the
         // hi and lo halves summed.
@@ -290,19 +294,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_apply(const __grid_constan
             mbar_arrive(smem_u32(&bar_acc_empty[ab]));
             __threadfence();
             __syncwarp();
-            const int tile = chunk / sc.chunks_row;
+            // this warp's 32 rows of the tile: the warp that writes them for the
+            // tile's last chunk sums them over the tile's chunks
+            const int tile = chunk / sc.chunks_row, cq = 2 + 4 * tile + quarter;
             int done = 0;
-            if (lane == 0) done = atomicAdd(&ctr[2 + tile], 1) == 4 * sc.chunks_row - 1;
+            if (lane == 0) done = atomicAdd(&ctr[cq], 1) == sc.chunks_row - 1;
             done = __shfl_sync(0xffffffffu, done, 0);
             if (!done) continue;
             __threadfence();
-            for (int q = 0; q < 4; ++q) {
-                const int r = q * 32 + lane, i = tile * BM + r;
+            {
+                const int i = tile * BM + row;
                 float acc[32];
 #pragma unroll
                 for (int k = 0; k < 32; ++k) acc[k] = 0.f;
                 for (int cc = tile * sc.chunks_row; cc < (tile + 1) * sc.chunks_row; ++cc) {
-                    const float4* src = reinterpret_cast<const float4*>(part + ((size_t)cc * BM + r) * 32);
+                    const float4* src = reinterpret_cast<const float4*>(part + ((size_t)cc * BM + row) * 32);
 #pragma unroll
                     for (int k = 0; k < 8; ++k) {
                         const float4 w = __ldcg(src + k);
@@ -320,7 +326,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_apply(const __grid_constan
                     }
                 }
             }
-            if (lane == 0) ctr[2 + tile] = 0;               // ready for the next launch
+            if (lane == 0) ctr[cq] = 0;                      // ready for the next launch
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -333,7 +339,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_apply(const __grid_constan
         __threadfence();
         if (atomicAdd(&ctr[1], 1) == (int)gridDim.x - 1) {
             if (*reinterpret_cast<volatile int*>(status) & 1)
-                for (int t2 = 0; t2 < sc.total / sc.chunks_row; ++t2) ctr[2 + t2] = 0;
+                for (int t2 = 0; t2 < 4 * (sc.total / sc.chunks_row); ++t2) ctr[2 + t2] = 0;
             ctr[0] = 0;
             ctr[1] = 0;
             __threadfence();
@@ -387,7 +393,7 @@ struct TcPlan {
     int stages = 5, ctas = 0;
     TcSched sc{};
     size_t part_bytes = 0;   // chunk partials: total x 128 x 32 FP32
-    size_t ctr_off = 0;      // byte offset of the counters (2 + row tiles ints)
+    size_t ctr_off = 0;      // byte offset of the counters (2 + 4 x row tiles ints)
     size_t bytes = 0;        // partials + counters
 };
 
@@ -406,7 +412,7 @@ TcPlan plan_for(int Nc, int ldk, int stages, int chunk_kb, int sm_count) {
     p.ctas = std::max(1, std::min(std::max(sm_count, 1), p.sc.total));
     p.part_bytes = sizeof(float) * (size_t)p.sc.total * BM * 32;
     p.ctr_off = (p.part_bytes + 255) / 256 * 256;
-    p.bytes = p.ctr_off + sizeof(int) * (size_t)(2 + tiles);
+    p.bytes = p.ctr_off + sizeof(int) * (size_t)(2 + 4 * tiles);
     return p;
 }
 
